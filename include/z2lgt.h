@@ -1,0 +1,224 @@
+/*
+ * z2lgt.h -- C ABI of the GB300 (sm_103a) state-vector library for the
+ * digital adiabatic simulation of quantum Z2 lattice gauge theory
+ * (Cui, Shi, Yang, "Circuit-based digital adiabatic quantum simulation and
+ * pseudoquantum simulation as new approaches to lattice gauge theory",
+ * arXiv:1910.08020, JHEP 2020).
+ *
+ * Model (Sec. 2.1, and the "start from the ground state of X, H = X + K Z"
+ * variant of Sec. 2.3 with K = s*lambda):
+ *
+ *     H(s) = -sum_l sigma^x_l - s * lambda * sum_p U_p,   U_p = prod_{l in p} sigma^z_l
+ *
+ * on a periodic d = 2 or 3 lattice with one qubit per link; the run starts in
+ * |+>^N and ramps s = t/T linearly from 0 to 1 over M Trotter steps of
+ * dt = T/M (Sec. 2.2: M = N_s * n, T = N_s * t_s, dt = t_s / n).
+ *
+ * Conventions shared by every call
+ *   - qubit l is bit l of the amplitude index; sigma^z|0> = |0>,
+ *     sigma^z|1> = -|1> (Sec. 2.1);
+ *   - site s = x + L_x (y + L_y z); link l(s, mu) = d*s + mu (mu = 0: +x,
+ *     1: +y, 2: +z); plaquette (s, mu < nu) = {l(s,mu), l(s+mu,nu),
+ *     l(s+nu,mu), l(s,nu)}, listed site-major then plane (01, 02, 12);
+ *     star(s) = {l(s,mu), l(s-mu,mu)};
+ *   - a state is 2^N amplitudes, interleaved (re, im), in DEVICE memory:
+ *     Z2_C64 = 2 x float (8 B per amplitude), Z2_C128 = 2 x double (16 B);
+ *     the buffer must be 256-byte aligned and is owned by the caller (the
+ *     library never frees caller memory); every state operation is in place;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); calls
+ *     enqueue work on it and, unless stated otherwise, return before the GPU
+ *     finishes; calls that return host results synchronise that stream;
+ *   - every call returns Z2_OK (0) or a negative Z2_ERR_* code; the message
+ *     of the last error on a context is z2_last_error(ctx).  No C++
+ *     exception, abort or exit crosses this interface.
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef Z2LGT_H
+#define Z2LGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define Z2_OK 0
+#define Z2_ERR_ARG (-1)            /* invalid argument (NULL, size, range)          */
+#define Z2_ERR_LATTICE (-2)        /* lattice not supported (d, L, qubit count)     */
+#define Z2_ERR_OOM (-3)            /* device or host allocation failed              */
+#define Z2_ERR_BUDGET (-4)         /* request exceeds the server's HBM budget       */
+#define Z2_ERR_CUDA (-5)           /* a CUDA runtime call failed                    */
+#define Z2_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up            */
+#define Z2_ERR_CANCELLED (-7)      /* the request was cancelled                     */
+#define Z2_ERR_NOT_FOUND (-8)      /* unknown server ticket                         */
+
+/* ---- enumerations --------------------------------------------------------- */
+#define Z2_FIRST_ORDER 0 /* Eq. (a): per step psi <- R(dt) D(lambda s_j dt) psi            */
+#define Z2_SYMMETRIC 1   /* Eq. (s): psi <- D(lambda s_j dt/2) R(dt) D(lambda s_{j-1} dt/2) psi */
+
+#define Z2_C64 0  /* complex64 state, FP32 arithmetic, FP64 angles and reductions */
+#define Z2_C128 1 /* complex128 state, FP64 throughout                            */
+
+#define Z2_SAMPLE_STD 0   /* symmetric halves at s_{j-1} and s_j (second order)              */
+#define Z2_SAMPLE_PAPER 1 /* both halves at s_j: the literal right-end rule of Sec. 2.2 (O(dt)) */
+
+/* mask kinds for z2_lattice_masks (bit l set = link l in the operator) */
+#define Z2_MASK_PLAQ 0       /* U_p, one per plaquette (Sec. 2.1)                         */
+#define Z2_MASK_STAR 1       /* Gauss-law G_s, one per site (Sec. 2.1)                    */
+#define Z2_MASK_WILSON_2X2 2 /* 2x2 loop at the origin, xy plane (XOR of its 4 plaquettes) */
+#define Z2_MASK_CONTOUR 3    /* contours c1, c2, c3: perimeters 4, 6, 8 (Sec. 3.1)        */
+#define Z2_MASK_W_MU 4       /* non-contractible Wilson lines W_mu, one per direction     */
+#define Z2_MASK_V_MU 5       /* 't Hooft operators V_mu: mu-links of the plane x_mu = 0   */
+
+/* z2_results.flags bits */
+#define Z2_FLAG_WILSON_DEGENERATE (1u << 0)  /* 2x2 loop wraps the torus: NaN reported */
+#define Z2_FLAG_CONTOUR_DEGENERATE (1u << 1) /* some contour wraps: NaN reported        */
+#define Z2_FLAG_NO_FIDELITY (1u << 2)        /* no reference state given: NaN           */
+
+/* sizes of the fixed arrays in z2_results */
+#define Z2_MAX_LINKS 34
+#define Z2_MAX_PLAQ 32
+#define Z2_MAX_SITES 32
+
+typedef struct z2_ctx z2_ctx;
+typedef struct z2_lattice z2_lattice;
+typedef struct z2_server z2_server;
+
+typedef struct {
+    int32_t d, L[3];
+    int32_t n_links; /* N = qubits = d * prod L  (Sec. 2.1)   */
+    int32_t n_plaq;  /* N_p = N (d - 1) / 2       (Sec. 2.1)  */
+    int32_t n_sites;
+} z2_lattice_info;
+
+/* Parameters of one adiabatic run (Sec. 2.2 and 2.3).  Caller-owned. */
+typedef struct {
+    double lambda;     /* coupling of the plaquette term at s = 1 (K = 1/g of Sec. 2.3) */
+    double T;          /* total evolution time (T = N_s t_s)                            */
+    int32_t M;         /* number of Trotter steps (M = N_s n), >= 1                     */
+    int32_t decomp;    /* Z2_FIRST_ORDER or Z2_SYMMETRIC                                */
+    int32_t precision; /* Z2_C64 or Z2_C128                                             */
+    int32_t sampling;  /* Z2_SAMPLE_STD or Z2_SAMPLE_PAPER                              */
+} z2_run_params;
+
+/* Observables of a state (Sec. 2.4), reductions in FP64.  Caller-owned.
+ * Arrays are filled up to n_plaq / n_sites / n_links / d entries. */
+typedef struct {
+    double s;                       /* ramp parameter the energy refers to         */
+    double energy;                  /* <H(s)> = -sum<sigma^x_l> - s lambda sum<U_p> */
+    double norm;                    /* <psi|psi>                                   */
+    double mean_plaq;               /* mean <U_p>                                  */
+    double wilson_2x2;              /* <W> of the 2x2 loop (NaN if degenerate)     */
+    double mean_star;               /* mean Gauss-law <G_s> (exactly 1 in theory)  */
+    double fidelity;                /* |<ref|psi>|^2 (NaN without a reference)     */
+    double plaq[Z2_MAX_PLAQ];       /* <U_p>                                       */
+    double star[Z2_MAX_SITES];      /* <G_s>                                       */
+    double sigmaz[Z2_MAX_LINKS];    /* <sigma^z_l>                                 */
+    double sigmax[Z2_MAX_LINKS];    /* <sigma^x_l>                                 */
+    double wmu[3];                  /* <W_mu>                                      */
+    double vmu[3];                  /* <V_mu>                                      */
+    double contours[3];             /* <W_c1>, <W_c2>, <W_c3>                      */
+    uint32_t flags;                 /* Z2_FLAG_* bits                              */
+    int32_t status;                 /* Z2_OK or the error of this run (batches)    */
+} z2_results;
+
+/* ---- context --------------------------------------------------------------
+ * A context binds one CUDA device and owns the library's device scratch
+ * (reduction partials, phase tables) and its cached execution plans. */
+int z2_ctx_create(int device, z2_ctx **out);
+int z2_ctx_destroy(z2_ctx *ctx);
+/* Message of the last failed call on ctx (ctx may be NULL for the last
+ * failure of z2_ctx_create / z2_lattice_create on this thread).  The string
+ * is owned by the library and valid until the next call on ctx. */
+const char *z2_last_error(const z2_ctx *ctx);
+/* Library version string (static storage). */
+const char *z2_version(void);
+
+/* Number of kernel launches this context has issued so far (all calls). */
+int z2_ctx_launch_count(const z2_ctx *ctx, uint64_t *out);
+/* Drop every cached execution plan (phase tables and pass lists); the next
+ * call rebuilds and re-uploads what it needs.  Synchronises the device. */
+int z2_ctx_flush_plans(z2_ctx *ctx);
+
+/* ---- lattice (Sec. 2.1) ---------------------------------------------------
+ * d in {2, 3}; each L_mu >= 2; N = d * prod(L) <= Z2_MAX_LINKS and fits the
+ * device.  Periodic boundaries only.  Host-only objects. */
+int z2_lattice_create(int32_t d, const int32_t *L, z2_lattice **out);
+int z2_lattice_destroy(z2_lattice *lat);
+int z2_lattice_info_get(const z2_lattice *lat, z2_lattice_info *out);
+/* Copies the masks of `kind` into out[0 .. cap), count in *n.  Returns
+ * Z2_ERR_ARG if cap is too small (then *n still holds the count). */
+int z2_lattice_masks(const z2_lattice *lat, int32_t kind, uint64_t *out, size_t cap, size_t *n);
+/* Bytes of a state of this lattice at `precision`. */
+int z2_state_bytes(const z2_lattice *lat, int32_t precision, size_t *bytes);
+
+/* ---- state preparation and the two layers of a step ---------------------- */
+/* psi <- |+>^N, every amplitude 2^{-N/2} (Sec. 2.3, ground state of X). */
+int z2_init_plus(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, void *stream);
+/* psi <- D(theta) psi, D(theta) = exp(i theta sum_p U_p): the whole plaquette
+ * layer as one diagonal pass (Eq. (ara) applied to every plaquette, Sec. 2.2). */
+int z2_apply_plaquettes(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state,
+                        double theta, void *stream);
+/* psi <- R(dt) psi, R(dt) = prod_l exp(i dt sigma^x_l) = prod_l R_x^l(-2 dt):
+ * the transverse-field layer (Sec. 2.2). */
+int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state,
+                      double dt, void *stream);
+/* psi <- H^{(x)N} psi (Hadamard on every qubit): maps sigma^x-type operators
+ * to sigma^z-type ones, "H sigma^z H" of Sec. 2.4.  Its own inverse. */
+int z2_apply_hadamard(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state,
+                      void *stream);
+
+/* ---- evolution (Sec. 2.2) -------------------------------------------------
+ * Applies steps j0+1 .. j1 (0 <= j0 <= j1 <= M) of the schedule of `p` to
+ * `state` in place.  A whole run is j0 = 0, j1 = M; cutting a run into
+ * segments is the paper's pause-measure-resume (Sec. 2.4) and equals the
+ * uncut run up to rounding.  Symmetric segments close with the half layer
+ * D(lambda s_{j1} dt / 2), so the state is at s = j1/M on return. */
+int z2_evolve(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, int32_t j0,
+              int32_t j1, void *stream);
+
+/* Shape of the execution plan z2_evolve uses for steps j0+1 .. j1: the
+ * qubits are split into n_groups groups of at most tile_bits qubits; each
+ * streaming pass over the state applies one group's gates (and at a step
+ * boundary the plaquette layer between two applications of the same group),
+ * so a step costs n_groups - 1 passes (1 when n_groups == 1, where the whole
+ * state is one tile and the run is a single launch). */
+typedef struct {
+    int32_t tile_bits;   /* qubits held by one CTA tile                      */
+    int32_t n_groups;    /* qubit groups                                     */
+    int32_t n_passes;    /* streaming passes over the state                  */
+    int32_t n_launches;  /* kernel launches of the segment                   */
+    int32_t n_tables;    /* phase tables (one per plaquette layer)           */
+    int32_t flip;        /* 1 if a final all-qubit sigma^x flip is applied   */
+} z2_plan_info;
+int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, int32_t j0, int32_t j1,
+                        z2_plan_info *out);
+
+/* ---- observables (Sec. 2.4) -----------------------------------------------
+ * Fills `out` for the state at ramp parameter s (energy = <H(s)>).  `ref` is
+ * an optional device state of the same size and precision for the fidelity
+ * |<ref|psi>|^2 (NULL: NaN and Z2_FLAG_NO_FIDELITY).  sigma^x-type
+ * quantities are measured as sigma^z after a Hadamard layer, which is undone
+ * before return, so `state` is unchanged up to rounding.  Synchronises
+ * `stream`. */
+int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, double s,
+               const void *ref, void *stream, z2_results *out);
+/* Whole run: z2_init_plus, z2_evolve(0, M), z2_measure(s = 1). */
+int z2_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state,
+           const void *ref, void *stream, z2_results *out);
+
+/* ---- raw reductions (Sec. 2.4) --------------------------------------------
+ * out[k] = sum_i |psi_i|^2 (-1)^{popcount(i & masks[k])} = <prod_{l in mask_k} sigma^z_l>
+ * for k < n_masks (host arrays), in FP64.  Synchronises `stream`. */
+int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state,
+             const uint64_t *masks, int32_t n_masks, double *out, void *stream);
+/* out[0] + i out[1] = <a|b> = sum_i conj(a_i) b_i, FP64.  Synchronises `stream`. */
+int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b,
+               double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* Z2LGT_H */

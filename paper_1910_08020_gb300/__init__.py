@@ -1,0 +1,331 @@
+"""Python binding of libz2lgt, the GB300 (sm_103a) state-vector library for
+the digital adiabatic simulation of quantum Z2 lattice gauge theory
+(Cui, Shi, Yang, arXiv:1910.08020).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library behind the C ABI of include/z2lgt.h.  Functions keep the C names
+(``z2_run``, ``z2_evolve``, ...).  States are CUDA tensors (complex64 or
+complex128, 256-byte aligned, owned by the caller); streams are
+``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers (default: the
+current PyTorch stream).  There is no CPU fallback: if the library is not
+built, loading fails with an error.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "Z2Error", "RunParams", "Results", "LatticeInfo", "load", "build",
+    "z2_ctx_create", "z2_ctx_destroy", "z2_last_error", "z2_version", "z2_ctx_launch_count",
+    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo",
+    "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
+    "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
+    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap",
+    "Context", "Lattice", "results_dict",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libz2lgt.so")
+
+Z2_OK = 0
+Z2_FIRST_ORDER, Z2_SYMMETRIC = 0, 1
+Z2_C64, Z2_C128 = 0, 1
+Z2_SAMPLE_STD, Z2_SAMPLE_PAPER = 0, 1
+Z2_MASK_PLAQ, Z2_MASK_STAR, Z2_MASK_WILSON_2X2, Z2_MASK_CONTOUR, Z2_MASK_W_MU, Z2_MASK_V_MU = range(6)
+Z2_FLAG_WILSON_DEGENERATE, Z2_FLAG_CONTOUR_DEGENERATE, Z2_FLAG_NO_FIDELITY = 1, 2, 4
+Z2_MAX_LINKS, Z2_MAX_PLAQ, Z2_MAX_SITES = 34, 32, 32
+ERRORS = {-1: "Z2_ERR_ARG", -2: "Z2_ERR_LATTICE", -3: "Z2_ERR_OOM", -4: "Z2_ERR_BUDGET", -5: "Z2_ERR_CUDA",
+          -6: "Z2_ERR_DEVICE_TIMEOUT", -7: "Z2_ERR_CANCELLED", -8: "Z2_ERR_NOT_FOUND"}
+
+
+class Z2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class RunParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("T", ctypes.c_double), ("M", ctypes.c_int32),
+                ("decomp", ctypes.c_int32), ("precision", ctypes.c_int32), ("sampling", ctypes.c_int32)]
+
+
+class LatticeInfo(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32 * 3), ("n_links", ctypes.c_int32),
+                ("n_plaq", ctypes.c_int32), ("n_sites", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("n_passes", ctypes.c_int32),
+                ("n_launches", ctypes.c_int32), ("n_tables", ctypes.c_int32), ("flip", ctypes.c_int32)]
+
+
+class Results(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_double), ("energy", ctypes.c_double), ("norm", ctypes.c_double),
+                ("mean_plaq", ctypes.c_double), ("wilson_2x2", ctypes.c_double), ("mean_star", ctypes.c_double),
+                ("fidelity", ctypes.c_double), ("plaq", ctypes.c_double * Z2_MAX_PLAQ),
+                ("star", ctypes.c_double * Z2_MAX_SITES), ("sigmaz", ctypes.c_double * Z2_MAX_LINKS),
+                ("sigmax", ctypes.c_double * Z2_MAX_LINKS), ("wmu", ctypes.c_double * 3),
+                ("vmu", ctypes.c_double * 3), ("contours", ctypes.c_double * 3), ("flags", ctypes.c_uint32),
+                ("status", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_D = ctypes.c_double
+
+_SIGS = {
+    "z2_ctx_create": [ctypes.c_int, ctypes.POINTER(_P)],
+    "z2_ctx_destroy": [_P],
+    "z2_ctx_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "z2_ctx_flush_plans": [_P],
+    "z2_evolve_plan_info": [_P, _P, ctypes.POINTER(RunParams), _I, _I, ctypes.POINTER(PlanInfo)],
+    "z2_last_error": [_P],
+    "z2_version": [],
+    "z2_lattice_create": [_I, ctypes.POINTER(_I), ctypes.POINTER(_P)],
+    "z2_lattice_destroy": [_P],
+    "z2_lattice_info_get": [_P, ctypes.POINTER(LatticeInfo)],
+    "z2_lattice_masks": [_P, _I, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "z2_state_bytes": [_P, _I, ctypes.POINTER(ctypes.c_size_t)],
+    "z2_init_plus": [_P, _P, _I, _P, _P],
+    "z2_apply_plaquettes": [_P, _P, _I, _P, _D, _P],
+    "z2_apply_rx_layer": [_P, _P, _I, _P, _D, _P],
+    "z2_apply_hadamard": [_P, _P, _I, _P, _P],
+    "z2_evolve": [_P, _P, ctypes.POINTER(RunParams), _P, _I, _I, _P],
+    "z2_measure": [_P, _P, ctypes.POINTER(RunParams), _P, _D, _P, _P, ctypes.POINTER(Results)],
+    "z2_run": [_P, _P, ctypes.POINTER(RunParams), _P, _P, _P, ctypes.POINTER(Results)],
+    "z2_zsums": [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
+    "z2_overlap": [_P, _I, _I, _P, _P, ctypes.POINTER(_D), _P],
+}
+
+
+def build(force=False, verbose=False):
+    """Compile libz2lgt.so in-tree (nvcc for sm_103a)."""
+    from . import buildlib as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+def load():
+    """Load libz2lgt.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libz2lgt.so is not built ({LIB_PATH}); run paper_1910_08020_gb300.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, argtypes in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = argtypes
+        f.restype = ctypes.c_char_p if name in ("z2_last_error", "z2_version") else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Device pointer of a tensor, or an int / None passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, ctx=None):
+    if rc != Z2_OK:
+        raise Z2Error(rc, load().z2_last_error(ctx).decode())
+
+
+# -- raw C-ABI mirrors (same names, argument marshalling only) ---------------------
+def z2_version():
+    return load().z2_version().decode()
+
+
+def z2_last_error(ctx=None):
+    return load().z2_last_error(ctx).decode()
+
+
+def z2_ctx_create(device=0):
+    out = _P()
+    _check(load().z2_ctx_create(device, ctypes.byref(out)))
+    return out.value
+
+
+def z2_ctx_destroy(ctx):
+    _check(load().z2_ctx_destroy(ctx))
+
+
+def z2_ctx_launch_count(ctx):
+    out = ctypes.c_uint64()
+    _check(load().z2_ctx_launch_count(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def z2_ctx_flush_plans(ctx):
+    _check(load().z2_ctx_flush_plans(ctx), ctx)
+
+
+def z2_evolve_plan_info(ctx, lat, params, j0, j1):
+    info = PlanInfo()
+    _check(load().z2_evolve_plan_info(ctx, lat, ctypes.byref(params), int(j0), int(j1), ctypes.byref(info)), ctx)
+    return info
+
+
+def z2_lattice_create(d, L):
+    arr = (_I * 3)(*(list(L) + [1] * (3 - len(L))))
+    out = _P()
+    _check(load().z2_lattice_create(d, arr, ctypes.byref(out)))
+    return out.value
+
+
+def z2_lattice_destroy(lat):
+    _check(load().z2_lattice_destroy(lat))
+
+
+def z2_lattice_info_get(lat):
+    info = LatticeInfo()
+    _check(load().z2_lattice_info_get(lat, ctypes.byref(info)))
+    return info
+
+
+def z2_lattice_masks(lat, kind):
+    n = ctypes.c_size_t()
+    buf = (ctypes.c_uint64 * 64)()
+    _check(load().z2_lattice_masks(lat, kind, buf, 64, ctypes.byref(n)))
+    return np.array(buf[:n.value], dtype=np.uint64)
+
+
+def z2_state_bytes(lat, precision):
+    n = ctypes.c_size_t()
+    _check(load().z2_state_bytes(lat, precision, ctypes.byref(n)))
+    return n.value
+
+
+def z2_init_plus(ctx, lat, precision, state, stream=None):
+    _check(load().z2_init_plus(ctx, lat, precision, _ptr(state), _stream(stream)), ctx)
+
+
+def z2_apply_plaquettes(ctx, lat, precision, state, theta, stream=None):
+    _check(load().z2_apply_plaquettes(ctx, lat, precision, _ptr(state), float(theta), _stream(stream)), ctx)
+
+
+def z2_apply_rx_layer(ctx, lat, precision, state, dt, stream=None):
+    _check(load().z2_apply_rx_layer(ctx, lat, precision, _ptr(state), float(dt), _stream(stream)), ctx)
+
+
+def z2_apply_hadamard(ctx, lat, precision, state, stream=None):
+    _check(load().z2_apply_hadamard(ctx, lat, precision, _ptr(state), _stream(stream)), ctx)
+
+
+def z2_evolve(ctx, lat, params, state, j0, j1, stream=None):
+    _check(load().z2_evolve(ctx, lat, ctypes.byref(params), _ptr(state), int(j0), int(j1), _stream(stream)), ctx)
+
+
+def z2_measure(ctx, lat, params, state, s=1.0, ref=None, stream=None):
+    res = Results()
+    _check(load().z2_measure(ctx, lat, ctypes.byref(params), _ptr(state), float(s), _ptr(ref), _stream(stream),
+                             ctypes.byref(res)), ctx)
+    return res
+
+
+def z2_run(ctx, lat, params, state, ref=None, stream=None):
+    res = Results()
+    _check(load().z2_run(ctx, lat, ctypes.byref(params), _ptr(state), _ptr(ref), _stream(stream),
+                         ctypes.byref(res)), ctx)
+    return res
+
+
+def z2_zsums(ctx, n_qubits, precision, state, masks, stream=None):
+    m = np.ascontiguousarray(masks, dtype=np.uint64)
+    out = np.zeros(len(m), dtype=np.float64)
+    _check(load().z2_zsums(ctx, n_qubits, precision, _ptr(state), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                           len(m), out.ctypes.data_as(ctypes.POINTER(_D)), _stream(stream)), ctx)
+    return out
+
+
+def z2_overlap(ctx, n_qubits, precision, a, b, stream=None):
+    out = np.zeros(2, dtype=np.float64)
+    _check(load().z2_overlap(ctx, n_qubits, precision, _ptr(a), _ptr(b), out.ctypes.data_as(ctypes.POINTER(_D)),
+                             _stream(stream)), ctx)
+    return complex(out[0], out[1])
+
+
+def results_dict(res, info):
+    """Results struct -> dict of numpy arrays trimmed to the lattice."""
+    d = {k: getattr(res, k) for k in ("s", "energy", "norm", "mean_plaq", "wilson_2x2", "mean_star", "fidelity",
+                                      "flags", "status")}
+    d["plaq"] = np.array(res.plaq[:info.n_plaq])
+    d["star"] = np.array(res.star[:info.n_sites])
+    d["sigmaz"] = np.array(res.sigmaz[:info.n_links])
+    d["sigmax"] = np.array(res.sigmax[:info.n_links])
+    d["wmu"] = np.array(res.wmu[:info.d])
+    d["vmu"] = np.array(res.vmu[:info.d])
+    d["contours"] = np.array(res.contours[:3])
+    return d
+
+
+# -- small object wrappers ---------------------------------------------------------
+class Context:
+    def __init__(self, device=0):
+        self.handle = z2_ctx_create(device)
+
+    def close(self):
+        if self.handle:
+            z2_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice:
+    def __init__(self, d, L):
+        self.handle = z2_lattice_create(d, L)
+        self.info = z2_lattice_info_get(self.handle)
+        self.d = self.info.d
+        self.n_links = self.info.n_links
+        self.n_plaq = self.info.n_plaq
+        self.n_sites = self.info.n_sites
+
+    def masks(self, kind):
+        return z2_lattice_masks(self.handle, kind)
+
+    def state_bytes(self, precision=Z2_C64):
+        return z2_state_bytes(self.handle, precision)
+
+    def close(self):
+        if self.handle:
+            z2_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def params(lam, T, M, decomp=Z2_SYMMETRIC, precision=Z2_C64, sampling=Z2_SAMPLE_STD):
+    return RunParams(float(lam), float(T), int(M), int(decomp), int(precision), int(sampling))

@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "z2lgt.h"
+
+namespace z2 {
+
+// ---------------------------------------------------------------------------
+// Lattice (Sec. 2.1): links, plaquettes, stars and loop masks, host side.
+struct Lattice {
+    int d = 0;
+    int L[3] = {1, 1, 1};
+    int n_sites = 0, n_links = 0, n_plaq = 0;
+    std::vector<uint64_t> plaq, star, wmu, vmu;
+    uint64_t wilson2x2 = 0;
+    bool wilson_degenerate = false;
+    uint64_t contour[3] = {0, 0, 0};
+    bool contour_degenerate[3] = {false, false, false};
+    // colmask[l]: bit p set when link l belongs to plaquette p
+    uint32_t colmask[64] = {};
+};
+bool build_lattice(int d, const int32_t *L, Lattice &out, std::string &err);
+
+// ---------------------------------------------------------------------------
+// One fused pass over the state (Sec. 2.2, both layers of a step).
+//
+// A pass streams the state once, tile by tile.  A tile holds 2^TB amplitudes:
+// tile bit i < c is global bit i (contiguous run of 2^c amplitudes), tile bit
+// i >= c is global bit b + i - c.  Inside the tile the pass applies, in order,
+//   rot1: the single-qubit gate on the tile bits of mask rot1,
+//   mid:  the plaquette phase table (D with the folded gate scale) or a
+//         real scale,
+//   rot2: the gate on the tile bits of mask rot2.
+enum PassOp : int { OP_RX_TAN = 0, OP_RX_GEN = 1, OP_HADAMARD = 2 };
+enum MidOp : int { MID_NONE = 0, MID_TABLE = 1, MID_SCALE = 2 };
+
+struct PassDesc {
+    int tb = 0;        // tile bits (template instantiation)
+    int c = 0, b = 0;  // tile geometry, b >= c, c == tb for a contiguous tile
+    uint32_t rot1 = 0, rot2 = 0;
+    int mid = MID_NONE;
+    int table = -1;    // index of the phase table (MID_TABLE)
+    double scale = 1;  // MID_SCALE
+};
+
+// Everything a pass kernel needs besides the state pointer.
+struct PassArgs {
+    int n;                 // qubits
+    int c, b;              // tile geometry
+    uint32_t rot1, rot2;   // rotation masks over tile bits
+    int mid;               // MidOp
+    int np1;               // n_plaq + 1 (table length)
+    double p0, p1;         // gate parameters: OP_RX_TAN: t = tan(dt); OP_RX_GEN: cos, sin
+    double scale;          // MID_SCALE factor
+    const void *table;     // device phase table (np1 complex of the state's type)
+    uint32_t tcol[16];     // per tile bit: plaquette-membership mask of its global bit
+    uint32_t colmask[64];  // per global bit (for the tile-id part)
+};
+
+// Launchers (kernels.cu).  All return the cudaError_t of the launch.
+// `steps` is a device array of PassStep (pass_kernel.cuh), `tables` a device
+// array of phase tables, (Z2_MAX_PLAQ + 1) amplitudes of the state's type each.
+cudaError_t launch_pass_steps(bool c128, int tb, int op, void *psi, const PassArgs &a, const void *steps,
+                              int n_steps, const void *tables, int grid, cudaStream_t st);
+int pass_threads(bool c128, int tb);
+size_t pass_smem(bool c128, int tb);
+cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream_t st);
+cudaError_t launch_flip_all(bool c128, void *state, int n, int grid, cudaStream_t st);
+// FP64 reductions over 2^n amplitudes (n >= 8): per-block partials in
+// `partials` (reduce_blocks(n) x outputs doubles), then a fixed-order final
+// sum into d_out (device).  zsums: 1 <= n_masks <= max_zsum_masks().
+cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
+                         double *d_out, cudaStream_t st);
+cudaError_t launch_overlap(bool c128, const void *a, const void *b, int n, double *partials, double *d_out,
+                           cudaStream_t st);
+int max_zsum_masks();
+int reduce_blocks(int n);
+
+struct PassStepHost {
+    uint32_t rot1, rot2;
+    int32_t mid, table;
+    double scale;
+};
+
+}  // namespace z2

@@ -1,0 +1,822 @@
+// Runtime and C ABI: contexts, execution plans, evolution, measurement.
+//
+// A run of the digital adiabatic algorithm (Sec. 2.2) is, in application
+// order, the operator sequence
+//
+//     D(theta_0)  R  D(theta_1)  R  ...  R  D(theta_M)
+//
+// with R = prod_l exp(i dt sigma^x_l) and D(theta) = exp(i theta sum_p U_p):
+//   first order (Eq. (a), varying factor first, right-end sampling):
+//       theta_k = lambda s_{k+1} dt (k < M), theta_M = 0
+//   symmetric (Eq. (s) with its halves merged as in the rewritten product of
+//   Sec. 2.2; trapezoid sampling, second order):
+//       theta_0 = 0, theta_k = lambda s_k dt, theta_M = lambda s_M dt / 2
+//   symmetric, the paper's literal sampling (both halves at s_j):
+//       theta_0 = lambda s_1 dt/2, theta_k = lambda (s_k + s_{k+1}) dt/2, theta_M = lambda dt/2
+// where s_k = k/M.  The plan splits the N qubits into groups that each fit
+// one tile, reverses the group order every step so that the last group of
+// step j and the first group of step j+1 share one pass with D(theta_j)
+// between them, and therefore streams the state g-1 times per step for g
+// groups (g >= 2).
+#include <cmath>
+#include <complex>
+#include <functional>
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+
+#include "internal.h"
+
+using z2::Lattice;
+
+struct z2_lattice {
+    Lattice lat;
+};
+
+namespace z2 {
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Group {
+    int lo = 0, hi = 0;  // global bits [lo, hi) rotated by this group
+    int c = 0, b = 0;    // tile geometry
+    uint32_t rot = 0;    // tile-bit mask of the group's bits
+};
+
+struct Geometry {
+    int n = 0, tb = 0;
+    bool c128 = false;
+    std::vector<Group> groups;
+    std::vector<int> order;  // application order within an even step
+};
+
+struct HostPass {
+    int group;
+    PassStepHost step;
+};
+
+// A compiled segment of a run (or a single layer): passes, tables, flip.
+struct Plan {
+    Geometry geo;
+    int op = OP_RX_TAN;
+    double gate = 0;  // tan(delta) for OP_RX_TAN
+    std::vector<HostPass> passes;
+    std::vector<std::complex<double>> tables;  // n_tables x (Z2_MAX_PLAQ + 1)
+    bool flip = false;
+    void *d_steps = nullptr;
+    void *d_tables = nullptr;
+    std::vector<PassArgs> args;  // per group
+    ~Plan() {
+        if (d_steps) cudaFree(d_steps);
+        if (d_tables) cudaFree(d_tables);
+    }
+};
+
+}  // namespace
+}  // namespace z2
+
+struct z2_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string last_error;
+    double *d_partials = nullptr;  // reduction partials (2^16 x 32 doubles)
+    double *d_out = nullptr;       // reduction outputs (256 doubles)
+    double *h_out = nullptr;       // pinned copy of d_out
+    std::map<std::string, std::unique_ptr<z2::Plan>> plans;
+    int tb_override = 0;
+    uint64_t launches = 0;
+};
+
+namespace z2 {
+namespace {
+
+constexpr int TABLE_STRIDE = Z2_MAX_PLAQ + 1;
+constexpr size_t PARTIALS_DOUBLES = (size_t(1) << 16) * 32;
+constexpr int OUT_DOUBLES = 256;
+
+int fail(z2_ctx *ctx, int code, const std::string &msg) {
+    if (ctx)
+        ctx->last_error = msg;
+    else
+        g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(z2_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, Z2_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define Z2_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int tile_limit(bool c128) { return c128 ? 13 : 14; }
+int regbits(bool c128) { return c128 ? 4 : 5; }
+
+// Choose the tile size and split the qubits into groups (see file comment).
+bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &err) {
+    g = Geometry{};
+    g.n = n;
+    g.c128 = c128;
+    const int R = regbits(c128);
+    if (n < 8) {
+        err = "states of fewer than 8 qubits are not supported";
+        return false;
+    }
+    if (n <= tile_limit(c128)) {
+        g.tb = n;
+        Group gr;
+        gr.lo = 0;
+        gr.hi = n;
+        gr.c = n;
+        gr.b = n;
+        gr.rot = (1u << n) - 1u;
+        g.groups.push_back(gr);
+        g.order = {0};
+        return true;
+    }
+    constexpr int CMIN = 3;  // >= 2^3 contiguous amplitudes per strided segment
+    int best_tb = 0, best_h = 1 << 30;
+    std::vector<int> cands;
+    if (tb_override)
+        cands.push_back(tb_override);
+    else
+        for (int tb = tile_limit(c128) - 2; tb <= tile_limit(c128); ++tb) cands.push_back(tb);
+    for (int tb : cands) {
+        if (tb < 8 || tb > tile_limit(c128) || tb >= n) continue;
+        const int rem = n - tb;
+        const int h = (rem + (tb - CMIN) - 1) / (tb - CMIN);
+        if (h < best_h) {
+            best_h = h;
+            best_tb = tb;
+        }
+    }
+    if (!best_tb) {
+        err = "no tile size fits this state";
+        return false;
+    }
+    const int tb = best_tb, h = best_h;
+    int n_low = tb, rem = n - tb;
+    if (rem < R * h) {  // only for h == 1: keep every high group >= R bits
+        n_low = n - R * h;
+        rem = R * h;
+    }
+    g.tb = tb;
+    Group low;
+    low.lo = 0;
+    low.hi = n_low;
+    low.c = tb;
+    low.b = tb;
+    low.rot = (n_low >= 32) ? 0xffffffffu : ((1u << n_low) - 1u);
+    g.groups.push_back(low);
+    int lo = n_low;
+    for (int i = 0; i < h; ++i) {
+        const int k = rem / h + (i < rem % h ? 1 : 0);
+        Group gr;
+        gr.lo = lo;
+        gr.hi = lo + k;
+        gr.c = tb - k;
+        gr.b = lo;
+        gr.rot = ((1u << k) - 1u) << gr.c;
+        if (gr.c < CMIN || gr.c > tb - R || gr.b < gr.c) {
+            err = "internal tile planning error";
+            return false;
+        }
+        g.groups.push_back(gr);
+        lo += k;
+    }
+    // low group in the middle so that the merged boundary passes are the
+    // cheaper strided ones
+    if (g.groups.size() >= 3) {
+        g.order.push_back(1);
+        g.order.push_back(0);
+        for (int i = 2; i < (int)g.groups.size(); ++i) g.order.push_back(i);
+    } else {
+        g.order = {0, 1};
+    }
+    return true;
+}
+
+PassArgs make_args(const Lattice &lat, const Geometry &g, const Group &gr) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = g.n;
+    a.c = gr.c;
+    a.b = gr.b;
+    a.np1 = lat.n_plaq + 1;
+    for (int i = 0; i < g.tb; ++i) {
+        const int gpos = i < gr.c ? i : gr.b + i - gr.c;
+        a.tcol[i] = gpos < 64 ? lat.colmask[gpos] : 0;
+    }
+    std::memcpy(a.colmask, lat.colmask, sizeof(a.colmask));
+    return a;
+}
+
+// Event list of a layer sequence: group applications and D events.
+struct Event {
+    int kind;  // 0 = group, 1 = D
+    int group;
+    int table;
+};
+
+void pack_passes(const std::vector<Event> &ev, const Geometry &g, std::vector<HostPass> &out) {
+    size_t i = 0;
+    while (i < ev.size()) {
+        HostPass p{};
+        p.group = 0;
+        p.step.mid = MID_NONE;
+        p.step.table = -1;
+        p.step.scale = 1.0;
+        if (ev[i].kind == 0) {
+            const int gi = ev[i].group;
+            p.group = gi;
+            p.step.rot1 = g.groups[gi].rot;
+            ++i;
+            if (i < ev.size() && ev[i].kind == 1) {
+                p.step.mid = MID_TABLE;
+                p.step.table = ev[i].table;
+                ++i;
+                if (i < ev.size() && ev[i].kind == 0 && ev[i].group == gi) {
+                    p.step.rot2 = g.groups[gi].rot;
+                    ++i;
+                }
+            }
+        } else {
+            p.step.mid = MID_TABLE;
+            p.step.table = ev[i].table;
+            ++i;
+            if (i < ev.size() && ev[i].kind == 0) {
+                p.group = ev[i].group;
+                p.step.rot2 = g.groups[p.group].rot;
+                ++i;
+            }
+        }
+        out.push_back(p);
+    }
+}
+
+// exp(i dt sigma^x) = (i^q cos(delta))^... per qubit: dt = q pi/2 + delta,
+// |delta| <= pi/4, exp(i dt sigma^x) = (i sigma^x)^q cos(delta) (1 + i tan(delta) sigma^x)
+struct GateSplit {
+    int q;
+    double delta, t, c;
+};
+GateSplit split_gate(double dt) {
+    GateSplit s;
+    const double q = std::nearbyint(dt / (M_PI / 2));
+    s.q = (int)std::fmod(q, 4.0);
+    if (s.q < 0) s.q += 4;
+    s.delta = dt - q * (M_PI / 2);
+    s.t = std::tan(s.delta);
+    s.c = std::cos(s.delta);
+    return s;
+}
+
+std::complex<double> ipow(int q) {
+    switch (((q % 4) + 4) % 4) {
+        case 0: return {1, 0};
+        case 1: return {0, 1};
+        case 2: return {-1, 0};
+        default: return {0, -1};
+    }
+}
+
+void push_table(Plan &P, const Lattice &lat, double theta, std::complex<double> scale) {
+    const int np = lat.n_plaq;
+    for (int k = 0; k < TABLE_STRIDE; ++k) {
+        std::complex<double> v(0, 0);
+        if (k <= np) v = scale * std::exp(std::complex<double>(0, theta * (np - 2 * k)));
+        P.tables.push_back(v);
+    }
+}
+
+int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
+    const bool c128 = P.geo.c128;
+    std::vector<PassStepHost> steps;
+    for (auto &hp : P.passes) steps.push_back(hp.step);
+    if (!steps.empty()) {
+        Z2_CUDA(ctx, cudaMalloc(&P.d_steps, steps.size() * sizeof(PassStepHost)));
+        Z2_CUDA(ctx, cudaMemcpy(P.d_steps, steps.data(), steps.size() * sizeof(PassStepHost), cudaMemcpyHostToDevice));
+    }
+    if (!P.tables.empty()) {
+        const size_t cnt = P.tables.size();
+        if (c128) {
+            std::vector<double2> t(cnt);
+            for (size_t i = 0; i < cnt; ++i) t[i] = make_double2(P.tables[i].real(), P.tables[i].imag());
+            Z2_CUDA(ctx, cudaMalloc(&P.d_tables, cnt * sizeof(double2)));
+            Z2_CUDA(ctx, cudaMemcpy(P.d_tables, t.data(), cnt * sizeof(double2), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float2> t(cnt);
+            for (size_t i = 0; i < cnt; ++i)
+                t[i] = make_float2((float)P.tables[i].real(), (float)P.tables[i].imag());
+            Z2_CUDA(ctx, cudaMalloc(&P.d_tables, cnt * sizeof(float2)));
+            Z2_CUDA(ctx, cudaMemcpy(P.d_tables, t.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice));
+        }
+    }
+    for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
+    for (auto &a : P.args) a.p0 = P.gate;
+    return Z2_OK;
+}
+
+// theta_k of the merged sequence for steps j0+1 .. j1 (k = j0 .. j1)
+double theta_at(const z2_run_params &p, int k, int j0, int j1) {
+    const double M = p.M, dt = p.T / p.M, lam = p.lambda;
+    auto s = [&](int j) { return j / M; };
+    if (p.decomp == Z2_FIRST_ORDER) return k < j1 ? lam * s(k + 1) * dt : 0.0;
+    if (p.sampling == Z2_SAMPLE_PAPER) {
+        if (k == j0) return lam * s(j0 + 1) * dt / 2;
+        if (k == j1) return lam * s(j1) * dt / 2;
+        return lam * (s(k) + s(k + 1)) * dt / 2;
+    }
+    if (k == j0) return lam * s(j0) * dt / 2;
+    if (k == j1) return lam * s(j1) * dt / 2;
+    return lam * s(k) * dt;
+}
+
+// Build the plan of steps j0+1 .. j1 (an empty plan when j0 == j1).
+int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, int j0, int j1, Plan &P) {
+    std::string err;
+    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ctx->tb_override, P.geo, err))
+        return fail(ctx, Z2_ERR_LATTICE, err);
+    P.op = OP_RX_TAN;
+    if (j1 == j0) return upload_plan(ctx, lat, P);
+    const GateSplit gs = split_gate(p.T / p.M);
+    P.gate = gs.t;
+    const auto &g = P.geo;
+    std::vector<Event> ev;
+    std::complex<double> pending(1, 0);  // gate scale since the last D
+    int n_tab = 0;
+    const double th0 = theta_at(p, j0, j0, j1);
+    if (th0 != 0.0) {
+        push_table(P, lat, th0, pending);
+        ev.push_back({1, 0, n_tab++});
+    }
+    for (int j = j0 + 1; j <= j1; ++j) {
+        const bool fwd = ((j - 1) & 1) == 0;
+        const int G = (int)g.order.size();
+        for (int k = 0; k < G; ++k) {
+            const int gi = g.order[fwd ? k : G - 1 - k];
+            ev.push_back({0, gi, -1});
+            const int bits = g.groups[gi].hi - g.groups[gi].lo;
+            pending *= std::pow(gs.c, bits) * ipow(gs.q * bits);
+        }
+        push_table(P, lat, theta_at(p, j, j0, j1), pending);
+        pending = {1, 0};
+        ev.push_back({1, 0, n_tab++});
+    }
+    pack_passes(ev, g, P.passes);
+    P.flip = (gs.q & 1) && ((j1 - j0) & 1);
+    return upload_plan(ctx, lat, P);
+}
+
+int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
+    const auto &g = P.geo;
+    const bool c128 = g.c128;
+    const uint64_t ntiles = 1ull << (g.n - g.tb);
+    const int grid = (int)std::min<uint64_t>(ntiles, 1u << 20);
+    const size_t step_bytes = sizeof(PassStepHost);
+    if (g.groups.size() == 1 && !P.passes.empty()) {
+        // single tile: the whole pass list in one launch, state held in registers
+        Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[0], P.d_steps, (int)P.passes.size(),
+                                       P.d_tables, grid, st));
+        ctx->launches += 1;
+    } else {
+        for (size_t i = 0; i < P.passes.size(); ++i) {
+            const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+            Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[P.passes[i].group], sp, 1, P.d_tables,
+                                           grid, st));
+        }
+        ctx->launches += P.passes.size();
+    }
+    if (P.flip) {
+        Z2_CUDA(ctx, launch_flip_all(c128, state, g.n, ctx->sm_count * 8, st));
+        ctx->launches += 1;
+    }
+    return Z2_OK;
+}
+
+std::string plan_key(const char *kind, const Lattice &lat, const z2_run_params *p, int a, int b, double x) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s|%d|%d,%d,%d|%a|%a|%d|%d|%d|%d|%d|%d|%a|%d", kind, lat.d, lat.L[0], lat.L[1],
+                  lat.L[2], p ? p->lambda : 0.0, p ? p->T : 0.0, p ? p->M : 0, p ? p->decomp : 0,
+                  p ? p->precision : 0, p ? p->sampling : 0, a, b, x, 0);
+    return buf;
+}
+
+int check_params(z2_ctx *ctx, const z2_run_params *p) {
+    if (!p) return fail(ctx, Z2_ERR_ARG, "run parameters are NULL");
+    if (p->M < 1) return fail(ctx, Z2_ERR_ARG, "M must be >= 1");
+    if (p->decomp != Z2_FIRST_ORDER && p->decomp != Z2_SYMMETRIC) return fail(ctx, Z2_ERR_ARG, "bad decomposition");
+    if (p->precision != Z2_C64 && p->precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (p->sampling != Z2_SAMPLE_STD && p->sampling != Z2_SAMPLE_PAPER) return fail(ctx, Z2_ERR_ARG, "bad sampling");
+    if (!std::isfinite(p->lambda) || !std::isfinite(p->T)) return fail(ctx, Z2_ERR_ARG, "lambda and T must be finite");
+    return Z2_OK;
+}
+
+int check_state(z2_ctx *ctx, const void *state) {
+    if (!state) return fail(ctx, Z2_ERR_ARG, "state pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(state) % 256) return fail(ctx, Z2_ERR_ARG, "state must be 256-byte aligned");
+    return Z2_OK;
+}
+
+Plan *get_plan(z2_ctx *ctx, const std::string &key) {
+    auto it = ctx->plans.find(key);
+    return it == ctx->plans.end() ? nullptr : it->second.get();
+}
+
+// Hadamard layer plan: every group once, scale 2^{-k/2} per group pass.
+int build_hadamard_plan(z2_ctx *ctx, const Lattice &lat, bool c128, Plan &P) {
+    std::string err;
+    if (!plan_geometry(lat.n_links, c128, ctx->tb_override, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+    P.op = OP_HADAMARD;
+    for (int gi = 0; gi < (int)P.geo.groups.size(); ++gi) {
+        HostPass hp{};
+        hp.group = gi;
+        hp.step.rot1 = P.geo.groups[gi].rot;
+        hp.step.rot2 = 0;
+        hp.step.mid = MID_SCALE;
+        hp.step.table = -1;
+        hp.step.scale = std::pow(2.0, -0.5 * (P.geo.groups[gi].hi - P.geo.groups[gi].lo));
+        P.passes.push_back(hp);
+    }
+    return upload_plan(ctx, lat, P);
+}
+
+int ensure_plan(z2_ctx *ctx, const std::string &key, Plan *&out, const std::function<int(Plan &)> &build) {
+    out = get_plan(ctx, key);
+    if (out) return Z2_OK;
+    auto P = std::make_unique<Plan>();
+    int rc = build(*P);
+    if (rc != Z2_OK) return rc;
+    out = P.get();
+    ctx->plans[key] = std::move(P);
+    return Z2_OK;
+}
+
+}  // namespace
+}  // namespace z2
+
+using namespace z2;
+
+extern "C" {
+
+const char *z2_version(void) { return "z2lgt 0.1 (sm_103a)"; }
+
+const char *z2_last_error(const z2_ctx *ctx) { return ctx ? ctx->last_error.c_str() : g_last_error.c_str(); }
+
+int z2_ctx_create(int device, z2_ctx **out) {
+    if (!out) return fail(nullptr, Z2_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, Z2_ERR_CUDA, std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, Z2_ERR_ARG, "no such CUDA device");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, Z2_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    auto ctx = std::make_unique<z2_ctx>();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_partials, PARTIALS_DOUBLES * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
+        if (ctx->d_partials) cudaFree(ctx->d_partials);
+        if (ctx->d_out) cudaFree(ctx->d_out);
+        return fail(nullptr, Z2_ERR_OOM, "context scratch allocation failed");
+    }
+    if (const char *s = std::getenv("Z2_TILE_BITS")) ctx->tb_override = std::atoi(s);
+    *out = ctx.release();
+    return Z2_OK;
+}
+
+int z2_ctx_destroy(z2_ctx *ctx) {
+    if (!ctx) return Z2_OK;
+    cudaSetDevice(ctx->device);
+    ctx->plans.clear();
+    if (ctx->d_partials) cudaFree(ctx->d_partials);
+    if (ctx->d_out) cudaFree(ctx->d_out);
+    if (ctx->h_out) cudaFreeHost(ctx->h_out);
+    delete ctx;
+    return Z2_OK;
+}
+
+int z2_ctx_launch_count(const z2_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    *out = ctx->launches;
+    return Z2_OK;
+}
+
+int z2_ctx_flush_plans(z2_ctx *ctx) {
+    if (!ctx) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    Z2_CUDA(ctx, cudaDeviceSynchronize());
+    ctx->plans.clear();
+    return Z2_OK;
+}
+
+int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, int32_t j0, int32_t j1,
+                        z2_plan_info *out) {
+    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_params(ctx, p)) return rc;
+    if (j0 < 0 || j1 > p->M || j0 > j1) return fail(ctx, Z2_ERR_ARG, "need 0 <= j0 <= j1 <= M");
+    Plan *P = nullptr;
+    const std::string key = plan_key("evolve", lat->lat, p, j0, j1, 0);
+    if (int rc = ensure_plan(ctx, key, P,
+                             [&](Plan &Q) { return build_evolve_plan(ctx, lat->lat, *p, j0, j1, Q); }))
+        return rc;
+    out->tile_bits = P->geo.tb;
+    out->n_groups = (int)P->geo.groups.size();
+    out->n_passes = (int)P->passes.size();
+    out->n_launches = (P->geo.groups.size() == 1 ? (P->passes.empty() ? 0 : 1) : (int)P->passes.size()) + (P->flip ? 1 : 0);
+    out->n_tables = (int)(P->tables.size() / TABLE_STRIDE);
+    out->flip = P->flip ? 1 : 0;
+    return Z2_OK;
+}
+
+int z2_lattice_create(int32_t d, const int32_t *L, z2_lattice **out) {
+    if (!out) return fail(nullptr, Z2_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    auto lat = std::make_unique<z2_lattice>();
+    std::string err;
+    if (!build_lattice(d, L, lat->lat, err)) return fail(nullptr, Z2_ERR_LATTICE, err);
+    *out = lat.release();
+    return Z2_OK;
+}
+
+int z2_lattice_destroy(z2_lattice *lat) {
+    delete lat;
+    return Z2_OK;
+}
+
+int z2_lattice_info_get(const z2_lattice *lat, z2_lattice_info *out) {
+    if (!lat || !out) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    out->d = lat->lat.d;
+    for (int i = 0; i < 3; ++i) out->L[i] = i < lat->lat.d ? lat->lat.L[i] : 1;
+    out->n_links = lat->lat.n_links;
+    out->n_plaq = lat->lat.n_plaq;
+    out->n_sites = lat->lat.n_sites;
+    return Z2_OK;
+}
+
+int z2_lattice_masks(const z2_lattice *lat, int32_t kind, uint64_t *out, size_t cap, size_t *n) {
+    if (!lat || !n) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    const Lattice &L = lat->lat;
+    std::vector<uint64_t> v;
+    switch (kind) {
+        case Z2_MASK_PLAQ: v = L.plaq; break;
+        case Z2_MASK_STAR: v = L.star; break;
+        case Z2_MASK_WILSON_2X2: v = {L.wilson2x2}; break;
+        case Z2_MASK_CONTOUR: v = {L.contour[0], L.contour[1], L.contour[2]}; break;
+        case Z2_MASK_W_MU: v = L.wmu; break;
+        case Z2_MASK_V_MU: v = L.vmu; break;
+        default: return fail(nullptr, Z2_ERR_ARG, "unknown mask kind");
+    }
+    *n = v.size();
+    if (cap < v.size() || (!out && !v.empty())) return fail(nullptr, Z2_ERR_ARG, "output capacity too small");
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
+    return Z2_OK;
+}
+
+int z2_state_bytes(const z2_lattice *lat, int32_t precision, size_t *bytes) {
+    if (!lat || !bytes) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(nullptr, Z2_ERR_ARG, "bad precision");
+    *bytes = (precision == Z2_C128 ? 16ull : 8ull) << lat->lat.n_links;
+    return Z2_OK;
+}
+
+int z2_init_plus(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, state)) return rc;
+    Z2_CUDA(ctx, launch_init_plus(precision == Z2_C128, state, lat->lat.n_links, ctx->sm_count * 16,
+                                  (cudaStream_t)stream));
+    ctx->launches += 1;
+    return Z2_OK;
+}
+
+int z2_evolve(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, int32_t j0, int32_t j1,
+              void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_params(ctx, p)) return rc;
+    if (int rc = check_state(ctx, state)) return rc;
+    if (j0 < 0 || j1 > p->M || j0 > j1) return fail(ctx, Z2_ERR_ARG, "need 0 <= j0 <= j1 <= M");
+    if (j0 == j1) return Z2_OK;
+    Plan *P = nullptr;
+    const std::string key = plan_key("evolve", lat->lat, p, j0, j1, 0);
+    if (int rc = ensure_plan(ctx, key, P,
+                             [&](Plan &Q) { return build_evolve_plan(ctx, lat->lat, *p, j0, j1, Q); }))
+        return rc;
+    return exec_plan(ctx, *P, state, (cudaStream_t)stream);
+}
+
+int z2_apply_plaquettes(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, double theta,
+                        void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, state)) return rc;
+    Plan *P = nullptr;
+    z2_run_params pp{};
+    pp.precision = precision;
+    const std::string key = plan_key("plaq", lat->lat, &pp, 0, 0, theta);
+    if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
+            std::string err;
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, Q.geo, err))
+                return fail(ctx, Z2_ERR_LATTICE, err);
+            Q.op = OP_RX_TAN;
+            push_table(Q, lat->lat, theta, {1, 0});
+            HostPass hp{};
+            hp.group = 0;
+            hp.step.mid = MID_TABLE;
+            hp.step.table = 0;
+            hp.step.scale = 1;
+            Q.passes.push_back(hp);
+            return upload_plan(ctx, lat->lat, Q);
+        }))
+        return rc;
+    return exec_plan(ctx, *P, state, (cudaStream_t)stream);
+}
+
+int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, double dt, void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (!std::isfinite(dt)) return fail(ctx, Z2_ERR_ARG, "dt must be finite");
+    if (int rc = check_state(ctx, state)) return rc;
+    Plan *P = nullptr;
+    z2_run_params pp{};
+    pp.precision = precision;
+    const std::string key = plan_key("rx", lat->lat, &pp, 0, 0, dt);
+    if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
+            std::string err;
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, Q.geo, err))
+                return fail(ctx, Z2_ERR_LATTICE, err);
+            Q.op = OP_RX_TAN;
+            const GateSplit gs = split_gate(dt);
+            Q.gate = gs.t;
+            std::vector<Event> ev;
+            std::complex<double> sc(1, 0);
+            for (int gi : Q.geo.order) {
+                ev.push_back({0, gi, -1});
+                const int bits = Q.geo.groups[gi].hi - Q.geo.groups[gi].lo;
+                sc *= std::pow(gs.c, bits) * ipow(gs.q * bits);
+            }
+            push_table(Q, lat->lat, 0.0, sc);
+            ev.push_back({1, 0, 0});
+            pack_passes(ev, Q.geo, Q.passes);
+            Q.flip = gs.q & 1;
+            return upload_plan(ctx, lat->lat, Q);
+        }))
+        return rc;
+    return exec_plan(ctx, *P, state, (cudaStream_t)stream);
+}
+
+int z2_apply_hadamard(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, state)) return rc;
+    Plan *P = nullptr;
+    z2_run_params pp{};
+    pp.precision = precision;
+    const std::string key = plan_key("had", lat->lat, &pp, 0, 0, 0);
+    if (int rc = ensure_plan(ctx, key, P,
+                             [&](Plan &Q) { return build_hadamard_plan(ctx, lat->lat, precision == Z2_C128, Q); }))
+        return rc;
+    return exec_plan(ctx, *P, state, (cudaStream_t)stream);
+}
+
+static int zsums_device(z2_ctx *ctx, int n, bool c128, const void *state, const uint64_t *masks, int n_masks,
+                        int out_off, cudaStream_t st) {
+    const int chunk = max_zsum_masks();
+    for (int k = 0; k < n_masks; k += chunk) {
+        const int m = std::min(chunk, n_masks - k);
+        Z2_CUDA(ctx, launch_zsums(c128, state, n, masks + k, m, ctx->d_partials, ctx->d_out + out_off + k, st));
+        ctx->launches += 2;
+    }
+    return Z2_OK;
+}
+
+int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state, const uint64_t *masks,
+             int32_t n_masks, double *out, void *stream) {
+    if (!ctx || !masks || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (n_qubits < 8 || n_qubits > Z2_MAX_LINKS) return fail(ctx, Z2_ERR_ARG, "need 8 <= n_qubits <= 34");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (n_masks < 0 || n_masks > OUT_DOUBLES) return fail(ctx, Z2_ERR_ARG, "need 0 <= n_masks <= 256");
+    if (int rc = check_state(ctx, state)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = zsums_device(ctx, n_qubits, precision == Z2_C128, state, masks, n_masks, 0, st)) return rc;
+    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, n_masks * sizeof(double), cudaMemcpyDeviceToHost, st));
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    std::memcpy(out, ctx->h_out, n_masks * sizeof(double));
+    return Z2_OK;
+}
+
+int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b, double *out,
+               void *stream) {
+    if (!ctx || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (n_qubits < 8 || n_qubits > Z2_MAX_LINKS) return fail(ctx, Z2_ERR_ARG, "need 8 <= n_qubits <= 34");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, a)) return rc;
+    if (int rc = check_state(ctx, b)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Z2_CUDA(ctx, launch_overlap(precision == Z2_C128, a, b, n_qubits, ctx->d_partials, ctx->d_out, st));
+    ctx->launches += 2;
+    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    out[0] = ctx->h_out[0];
+    out[1] = ctx->h_out[1];
+    return Z2_OK;
+}
+
+int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, double s, const void *ref,
+               void *stream, z2_results *out) {
+    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_params(ctx, p)) return rc;
+    if (int rc = check_state(ctx, state)) return rc;
+    if (ref)
+        if (int rc = check_state(ctx, ref)) return rc;
+    const Lattice &L = lat->lat;
+    const int n = L.n_links, np = L.n_plaq;
+    const bool c128 = p->precision == Z2_C128;
+    cudaStream_t st = (cudaStream_t)stream;
+    // sigma^z-type: norm, plaquettes, 2x2 loop, contours, W_mu, sigma^z_l
+    std::vector<uint64_t> zm;
+    zm.push_back(0);
+    for (auto m : L.plaq) zm.push_back(m);
+    zm.push_back(L.wilson2x2);
+    for (int k = 0; k < 3; ++k) zm.push_back(L.contour[k]);
+    for (auto m : L.wmu) zm.push_back(m);
+    for (int l = 0; l < n; ++l) zm.push_back(uint64_t(1) << l);
+    // sigma^x-type after the Hadamard layer: sigma^x_l, stars, V_mu
+    std::vector<uint64_t> xm;
+    for (int l = 0; l < n; ++l) xm.push_back(uint64_t(1) << l);
+    for (auto m : L.star) xm.push_back(m);
+    for (auto m : L.vmu) xm.push_back(m);
+    const int nz = (int)zm.size(), nx = (int)xm.size();
+    const int off_fid = nz + nx;
+    if (off_fid + 2 > OUT_DOUBLES) return fail(ctx, Z2_ERR_LATTICE, "too many observables");
+    if (int rc = zsums_device(ctx, n, c128, state, zm.data(), nz, 0, st)) return rc;
+    if (ref) {
+        Z2_CUDA(ctx, launch_overlap(c128, ref, state, n, ctx->d_partials, ctx->d_out + off_fid, st));
+        ctx->launches += 2;
+    }
+    if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
+    if (int rc = zsums_device(ctx, n, c128, state, xm.data(), nx, nz, st)) return rc;
+    if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
+    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, (off_fid + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    const double *h = ctx->h_out;
+    std::memset(out, 0, sizeof(*out));
+    const double nan = std::nan("");
+    out->s = s;
+    out->norm = h[0];
+    double sp = 0;
+    for (int k = 0; k < np; ++k) {
+        out->plaq[k] = h[1 + k];
+        sp += h[1 + k];
+    }
+    out->mean_plaq = sp / np;
+    out->wilson_2x2 = L.wilson_degenerate ? nan : h[1 + np];
+    if (L.wilson_degenerate) out->flags |= Z2_FLAG_WILSON_DEGENERATE;
+    for (int k = 0; k < 3; ++k) {
+        out->contours[k] = L.contour_degenerate[k] ? nan : h[2 + np + k];
+        if (L.contour_degenerate[k]) out->flags |= Z2_FLAG_CONTOUR_DEGENERATE;
+    }
+    for (int mu = 0; mu < L.d; ++mu) out->wmu[mu] = h[5 + np + mu];
+    for (int l = 0; l < n; ++l) out->sigmaz[l] = h[5 + np + L.d + l];
+    double sx = 0;
+    for (int l = 0; l < n; ++l) {
+        out->sigmax[l] = h[nz + l];
+        sx += h[nz + l];
+    }
+    double ss = 0;
+    for (int k = 0; k < L.n_sites; ++k) {
+        out->star[k] = h[nz + n + k];
+        ss += h[nz + n + k];
+    }
+    out->mean_star = ss / L.n_sites;
+    for (int mu = 0; mu < L.d; ++mu) out->vmu[mu] = h[nz + n + L.n_sites + mu];
+    out->energy = -sx - s * p->lambda * sp;
+    if (ref) {
+        out->fidelity = h[off_fid] * h[off_fid] + h[off_fid + 1] * h[off_fid + 1];
+    } else {
+        out->fidelity = nan;
+        out->flags |= Z2_FLAG_NO_FIDELITY;
+    }
+    out->status = Z2_OK;
+    return Z2_OK;
+}
+
+int z2_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, const void *ref, void *stream,
+           z2_results *out) {
+    if (int rc = check_params(ctx, p)) return rc;
+    if (int rc = z2_init_plus(ctx, lat, p->precision, state, stream)) return rc;
+    if (int rc = z2_evolve(ctx, lat, p, state, 0, p->M, stream)) return rc;
+    return z2_measure(ctx, lat, p, state, 1.0, ref, stream, out);
+}
+
+}  // extern "C"
