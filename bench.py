@@ -36,6 +36,9 @@ WORKLOADS = {
                 name="2+1D Z2 LGT 4x3 periodic, 24 link qubits, complex64, lambda=3, T=20, M=500"),
     "2x2x2": dict(d=3, L=(2, 2, 2), lam=1.0, T=15.0, M=300,
                   name="3+1D Z2 LGT 2x2x2 periodic, 24 link qubits, complex64, lambda=1, T=15, M=300"),
+    # small case of the 32-qubit kernel for profiler captures (2.1 GB state)
+    "7x2": dict(d=2, L=(7, 2), lam=3.0, T=2.0, M=20,
+                name="2+1D Z2 LGT 7x2 periodic, 28 link qubits, complex64 (2.1 GB), lambda=3, T=2, M=20"),
 }
 METRIC = "Trotter steps/s"
 

@@ -104,7 +104,10 @@ typedef struct {
 } z2_run_params;
 
 /* Observables of a state (Sec. 2.4), reductions in FP64.  Caller-owned.
- * Arrays are filled up to n_plaq / n_sites / n_links / d entries. */
+ * Expectation values are <psi|O|psi> / <psi|psi> and the fidelity is
+ * |<ref|psi>|^2 / (<ref|ref> <psi|psi>); `norm` is <psi|psi> as measured
+ * (1 up to rounding).  Arrays are filled up to n_plaq / n_sites / n_links / d
+ * entries. */
 typedef struct {
     double s;                       /* ramp parameter the energy refers to         */
     double energy;                  /* <H(s)> = -sum<sigma^x_l> - s lambda sum<U_p> */
@@ -112,7 +115,7 @@ typedef struct {
     double mean_plaq;               /* mean <U_p>                                  */
     double wilson_2x2;              /* <W> of the 2x2 loop (NaN if degenerate)     */
     double mean_star;               /* mean Gauss-law <G_s> (exactly 1 in theory)  */
-    double fidelity;                /* |<ref|psi>|^2 (NaN without a reference)     */
+    double fidelity;                /* normalised |<ref|psi>|^2 (NaN without ref)  */
     double plaq[Z2_MAX_PLAQ];       /* <U_p>                                       */
     double star[Z2_MAX_SITES];      /* <G_s>                                       */
     double sigmaz[Z2_MAX_LINKS];    /* <sigma^z_l>                                 */

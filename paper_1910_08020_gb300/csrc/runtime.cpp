@@ -757,52 +757,59 @@ int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void 
     for (auto m : L.star) xm.push_back(m);
     for (auto m : L.vmu) xm.push_back(m);
     const int nz = (int)zm.size(), nx = (int)xm.size();
-    const int off_fid = nz + nx;
-    if (off_fid + 2 > OUT_DOUBLES) return fail(ctx, Z2_ERR_LATTICE, "too many observables");
+    const int off_fid = nz + nx;  // <ref|psi> (2 doubles), then <ref|ref> (2 doubles)
+    if (off_fid + 4 > OUT_DOUBLES) return fail(ctx, Z2_ERR_LATTICE, "too many observables");
     if (int rc = zsums_device(ctx, n, c128, state, zm.data(), nz, 0, st)) return rc;
     if (ref) {
         Z2_CUDA(ctx, launch_overlap(c128, ref, state, n, ctx->d_partials, ctx->d_out + off_fid, st));
-        ctx->launches += 2;
+        Z2_CUDA(ctx, launch_overlap(c128, ref, ref, n, ctx->d_partials, ctx->d_out + off_fid + 2, st));
+        ctx->launches += 4;
     }
     if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
     if (int rc = zsums_device(ctx, n, c128, state, xm.data(), nx, nz, st)) return rc;
     if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
-    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, (off_fid + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, (off_fid + 4) * sizeof(double), cudaMemcpyDeviceToHost, st));
     Z2_CUDA(ctx, cudaStreamSynchronize(st));
     const double *h = ctx->h_out;
     std::memset(out, 0, sizeof(*out));
     const double nan = std::nan("");
+    // expectation values <psi|O|psi> / <psi|psi>: the norm differs from 1 only
+    // by rounding, and is reported as measured
+    const double nrm = h[0];
+    const double inv = nrm > 0 ? 1.0 / nrm : nan;
     out->s = s;
-    out->norm = h[0];
+    out->norm = nrm;
     double sp = 0;
     for (int k = 0; k < np; ++k) {
-        out->plaq[k] = h[1 + k];
-        sp += h[1 + k];
+        out->plaq[k] = h[1 + k] * inv;
+        sp += out->plaq[k];
     }
     out->mean_plaq = sp / np;
-    out->wilson_2x2 = L.wilson_degenerate ? nan : h[1 + np];
+    out->wilson_2x2 = L.wilson_degenerate ? nan : h[1 + np] * inv;
     if (L.wilson_degenerate) out->flags |= Z2_FLAG_WILSON_DEGENERATE;
     for (int k = 0; k < 3; ++k) {
-        out->contours[k] = L.contour_degenerate[k] ? nan : h[2 + np + k];
+        out->contours[k] = L.contour_degenerate[k] ? nan : h[2 + np + k] * inv;
         if (L.contour_degenerate[k]) out->flags |= Z2_FLAG_CONTOUR_DEGENERATE;
     }
-    for (int mu = 0; mu < L.d; ++mu) out->wmu[mu] = h[5 + np + mu];
-    for (int l = 0; l < n; ++l) out->sigmaz[l] = h[5 + np + L.d + l];
+    for (int mu = 0; mu < L.d; ++mu) out->wmu[mu] = h[5 + np + mu] * inv;
+    for (int l = 0; l < n; ++l) out->sigmaz[l] = h[5 + np + L.d + l] * inv;
     double sx = 0;
     for (int l = 0; l < n; ++l) {
-        out->sigmax[l] = h[nz + l];
-        sx += h[nz + l];
+        out->sigmax[l] = h[nz + l] * inv;
+        sx += out->sigmax[l];
     }
     double ss = 0;
     for (int k = 0; k < L.n_sites; ++k) {
-        out->star[k] = h[nz + n + k];
-        ss += h[nz + n + k];
+        out->star[k] = h[nz + n + k] * inv;
+        ss += out->star[k];
     }
     out->mean_star = ss / L.n_sites;
-    for (int mu = 0; mu < L.d; ++mu) out->vmu[mu] = h[nz + n + L.n_sites + mu];
+    for (int mu = 0; mu < L.d; ++mu) out->vmu[mu] = h[nz + n + L.n_sites + mu] * inv;
     out->energy = -sx - s * p->lambda * sp;
     if (ref) {
-        out->fidelity = h[off_fid] * h[off_fid] + h[off_fid + 1] * h[off_fid + 1];
+        // |<ref|psi>|^2 / (<ref|ref> <psi|psi>)
+        const double rn = h[off_fid + 2];
+        out->fidelity = (h[off_fid] * h[off_fid] + h[off_fid + 1] * h[off_fid + 1]) / (rn * nrm);
     } else {
         out->fidelity = nan;
         out->flags |= Z2_FLAG_NO_FIDELITY;

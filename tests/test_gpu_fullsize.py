@@ -79,7 +79,7 @@ def test_against_dual(ctx, L, decomp):
     psi_x = g[xs].cpu().numpy().astype(np.complex128)
     # each x configuration arises from tau and -tau: sum over tau / 2 with weight sqrt(2) phi(tau)
     ov = np.sum(np.conj(np.sqrt(2.0) * phi_d) * psi_x) / 2.0
-    F = abs(ov) ** 2
-    assert abs(F - F_ref) < 1e-6, (F, F_ref)
+    F = abs(ov) ** 2 / d["norm"]
+    assert abs(F - F_ref) < 1e-6, (F, F_ref, d["norm"], abs(ov) ** 2)
     del g
     torch.cuda.empty_cache()
