@@ -145,6 +145,12 @@ int z2_ctx_launch_count(const z2_ctx *ctx, uint64_t *out);
  * call rebuilds and re-uploads what it needs.  Synchronises the device. */
 int z2_ctx_flush_plans(z2_ctx *ctx);
 
+/* Execution options of a context (they change how, not what, is computed).
+ * Setting one drops the cached plans. */
+#define Z2_OPT_TILE_BITS 0    /* 0 = automatic, else amplitudes per tile = 2^value (8..14)   */
+#define Z2_OPT_PASS_VARIANT 1 /* 0 = automatic, 1 = direct global loads, 2 = TMA-pipelined   */
+int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
+
 /* ---- lattice (Sec. 2.1) ---------------------------------------------------
  * d in {2, 3}; each L_mu >= 2; N = d * prod(L) <= Z2_MAX_LINKS and fits the
  * device.  Periodic boundaries only.  Host-only objects. */

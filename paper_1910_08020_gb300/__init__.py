@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "Z2Error", "RunParams", "Results", "LatticeInfo", "load", "build",
     "z2_ctx_create", "z2_ctx_destroy", "z2_last_error", "z2_version", "z2_ctx_launch_count",
-    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo",
+    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_ctx_set_option",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
     "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap",
@@ -83,6 +83,7 @@ _SIGS = {
     "z2_ctx_destroy": [_P],
     "z2_ctx_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "z2_ctx_flush_plans": [_P],
+    "z2_ctx_set_option": [_P, _I, _I],
     "z2_evolve_plan_info": [_P, _P, ctypes.POINTER(RunParams), _I, _I, ctypes.POINTER(PlanInfo)],
     "z2_last_error": [_P],
     "z2_version": [],
@@ -172,6 +173,13 @@ def z2_ctx_launch_count(ctx):
     out = ctypes.c_uint64()
     _check(load().z2_ctx_launch_count(ctx, ctypes.byref(out)), ctx)
     return out.value
+
+
+Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT = 0, 1
+
+
+def z2_ctx_set_option(ctx, option, value):
+    _check(load().z2_ctx_set_option(ctx, int(option), int(value)), ctx)
 
 
 def z2_ctx_flush_plans(ctx):

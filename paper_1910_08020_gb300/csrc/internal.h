@@ -60,6 +60,7 @@ struct PassArgs {
     double p0, p1;         // gate parameters: OP_RX_TAN: t = tan(dt); OP_RX_GEN: cos, sin
     double scale;          // MID_SCALE factor
     const void *table;     // device phase table (np1 complex of the state's type)
+    int tma_lo_bits;       // tile-id bits below the strided part (b - c of the TMA view)
     uint32_t tcol[16];     // per tile bit: plaquette-membership mask of its global bit
     uint32_t colmask[64];  // per global bit (for the tile-id part)
 };
@@ -70,6 +71,13 @@ struct PassArgs {
 cudaError_t launch_pass_steps(bool c128, int tb, int op, void *psi, const PassArgs &a, const void *steps,
                               int n_steps, const void *tables, int grid, cudaStream_t st);
 int pass_threads(bool c128, int tb);
+// TMA-pipelined persistent variant: `tmap` is a CUtensorMap (5-D view of the
+// state, see make_tensor_map in runtime.cpp); `err` a device flag set to 1 if
+// a bounded wait gave up.
+cudaError_t launch_pass_tma(bool c128, int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
+                            int n_steps, const void *tables, int *err, int grid, cudaStream_t st);
+int tma_tile_limit(bool c128);
+int tma_smem_bytes(bool c128, int tb);
 size_t pass_smem(bool c128, int tb);
 cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream_t st);
 cudaError_t launch_flip_all(bool c128, void *state, int n, int grid, cudaStream_t st);

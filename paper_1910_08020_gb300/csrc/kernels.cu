@@ -21,6 +21,22 @@ cudaError_t launch_pass_steps(bool c128, int tb, int op, void *psi, const PassAr
                 : launch_pass_c64(tb, op, psi, a, steps, n_steps, tables, grid, st);
 }
 
+cudaError_t launch_pass_tma_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps, int n_steps,
+                                const void *tables, int *err, int grid, cudaStream_t st);
+cudaError_t launch_pass_tma_c128(int tb, int op, const PassArgs &a, const void *tmap, const void *steps, int n_steps,
+                                 const void *tables, int *err, int grid, cudaStream_t st);
+int tma_smem_bytes_c64(int tb);
+int tma_smem_bytes_c128(int tb);
+
+cudaError_t launch_pass_tma(bool c128, int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
+                            int n_steps, const void *tables, int *err, int grid, cudaStream_t st) {
+    return c128 ? launch_pass_tma_c128(tb, op, a, tmap, steps, n_steps, tables, err, grid, st)
+                : launch_pass_tma_c64(tb, op, a, tmap, steps, n_steps, tables, err, grid, st);
+}
+
+int tma_tile_limit(bool c128) { return c128 ? 12 : 13; }
+int tma_smem_bytes(bool c128, int tb) { return c128 ? tma_smem_bytes_c128(tb) : tma_smem_bytes_c64(tb); }
+
 int pass_threads(bool c128, int tb) { return 1 << (tb - (c128 ? Cfg<double2>::R : Cfg<float2>::R)); }
 size_t pass_smem(bool c128, int tb) {
     const int R = c128 ? Cfg<double2>::R : Cfg<float2>::R;

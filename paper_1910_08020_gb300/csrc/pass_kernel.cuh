@@ -301,3 +301,179 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, Tile<C, TB>::MINB) pass_kerne
 }
 
 }  // namespace z2
+
+// ---------------------------------------------------------------------------
+// TMA-pipelined variant (persistent CTAs).  Each CTA walks its tiles with a
+// two-stage ring of shared-memory buffers: while the registers of tile i are
+// being transformed, the tensor-memory-access unit already streams tile i+1
+// into the other buffer (cp.async.bulk.tensor, completion on an mbarrier), and
+// finished tiles leave through a TMA store.  The buffer of the tile being
+// transformed doubles as the scratch of its register-layout changes.
+#include <cuda.h>
+
+namespace z2 {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c1, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %2, %2, "
+        "%4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, const void *src, int c1, int c4) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %1, %1, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(0), "r"(c1), "r"(c4), "r"(smem_u32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Upper bound on mbarrier polls before a wait is declared failed (each poll
+// may suspend the thread for a while; far beyond any legitimate copy).
+constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;
+
+template <typename C, int TB>
+struct TmaTile {
+    using T = Tile<C, TB>;
+    static constexpr uint32_t TILE_BYTES = sizeof(C) << TB;
+    static constexpr uint32_t BUF_BYTES = ((sizeof(C) * T::SMEM_SLOTS + 1023) / 1024) * 1024;
+    static constexpr uint32_t SMEM_BYTES = 2 * BUF_BYTES + 1024;  // + alignment slack
+};
+
+// TMA tile coordinates: the tensor map views the state as
+// (x_lo, tile_lo, x_hi1, x_hi2, tile_hi); a tile is (0, t_lo, 0, 0, t_hi).
+template <typename C, int TB, int OP>
+__global__ void __launch_bounds__(Tile<C, TB>::NT, 1)
+    pass_kernel_tma(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
+                    const PassStep *__restrict__ steps, int n_steps, const C *__restrict__ tables, int *err) {
+    using T = Tile<C, TB>;
+    using TT = TmaTile<C, TB>;
+    using real = typename Cfg<C>::real;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ C tab[Z2_MAX_PLAQ + 1];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    auto buf = [&](int k) { return reinterpret_cast<C *>(base + k * TT::BUF_BYTES); };
+
+    const uint32_t t = threadIdx.x;
+    const real gate = (real)a.p0;
+    const uint64_t ntiles = 1ull << (a.n - TB);
+    const int lo_bits = a.tma_lo_bits;      // tile-id bits below the strided part
+    const int c = a.c, b = a.b, hib = b + TB - c;
+
+    if (t == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint64_t tile = blockIdx.x;
+    if (t == 0 && tile < ntiles) {
+        mbar_expect_tx(&mbar[0], TT::TILE_BYTES);
+        tma_load_5d(buf(0), &tmap, &mbar[0], (int)(tile & ((1ull << lo_bits) - 1)), (int)(tile >> lo_bits));
+    }
+    for (uint32_t i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int cur = i & 1;
+        const uint64_t next = tile + gridDim.x;
+        const bool has_next = next < ntiles;
+        if (t == 0 && has_next) {
+            bulk_wait_read_all();  // the store that last read buf(cur ^ 1) is done with it
+            fence_proxy_async();
+            mbar_expect_tx(&mbar[cur ^ 1], TT::TILE_BYTES);
+            tma_load_5d(buf(cur ^ 1), &tmap, &mbar[cur ^ 1], (int)(next & ((1ull << lo_bits) - 1)),
+                        (int)(next >> lo_bits));
+        }
+        // bounded wait for this tile's data
+        bool ok = false;
+        for (uint32_t k = 0; k < MBAR_POLL_LIMIT; ++k)
+            if ((ok = mbar_try_wait(&mbar[cur], (i >> 1) & 1))) break;
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(err, 1);
+                // let the copies in flight finish (bounded) before leaving
+                if (has_next)
+                    for (uint32_t k = 0; k < MBAR_POLL_LIMIT && !mbar_try_wait(&mbar[cur ^ 1], ((i + 1) >> 1) & 1);
+                         ++k) {
+                    }
+                bulk_wait_all();
+            }
+            return;
+        }
+        // plaquette parity of the tile-id bits
+        const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
+        const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
+
+        C *sm = buf(cur);
+        C v[T::NE];
+#pragma unroll
+        for (int j = 0; j < T::NE; ++j) v[j] = sm[t | ((uint32_t)j << T::r0(0))];
+        __syncthreads();  // dense reads done before the padded layout reuses the buffer
+
+        for (int s = 0; s < n_steps; ++s) {
+            const PassStep st = steps[s];
+            if (st.mid == MID_TABLE) {
+                __syncthreads();
+                for (uint32_t q = t; q < (uint32_t)a.np1; q += T::NT)
+                    tab[q] = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
+                __syncthreads();
+            }
+            int cur_l = 0;
+            rotate_in<C, TB, OP>(0, v, st.rot1, gate);
+#pragma unroll
+            for (int q = 1; q < T::K; ++q) {
+                if (st.rot1 & T::owned(q)) {
+                    relayout_rt<C, TB>(cur_l, q, v, sm, t);
+                    cur_l = q;
+                    rotate_in<C, TB, OP>(q, v, st.rot1, gate);
+                }
+            }
+            mid_in<C, TB>(cur_l, v, a, st.mid, st.scale, ptile, t, tab);
+            rotate_in<C, TB, OP>(cur_l, v, st.rot2, gate);
+            const int first = cur_l;
+#pragma unroll
+            for (int q = T::K - 1; q >= 1; --q) {
+                if (q != first && (st.rot2 & T::owned(q))) {
+                    relayout_rt<C, TB>(cur_l, q, v, sm, t);
+                    cur_l = q;
+                    rotate_in<C, TB, OP>(q, v, st.rot2, gate);
+                }
+            }
+            if (cur_l != 0) {
+                relayout_rt<C, TB>(cur_l, 0, v, sm, t);
+                if (first != 0) rotate_in<C, TB, OP>(0, v, st.rot2, gate);
+            }
+        }
+        __syncthreads();  // padded reads done before the dense store image is written
+#pragma unroll
+        for (int j = 0; j < T::NE; ++j) sm[t | ((uint32_t)j << T::r0(0))] = v[j];
+        fence_proxy_async();
+        __syncthreads();
+        if (t == 0) tma_store_5d(&tmap, sm, (int)(tile & ((1ull << lo_bits) - 1)), (int)(tile >> lo_bits));
+    }
+    if (t == 0) bulk_wait_all();
+}
+
+}  // namespace z2

@@ -30,6 +30,9 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 
 using z2::Lattice;
@@ -72,6 +75,9 @@ struct Plan {
     void *d_steps = nullptr;
     void *d_tables = nullptr;
     std::vector<PassArgs> args;  // per group
+    bool tma = false;                  // TMA-pipelined persistent kernel
+    const void *tmap_state = nullptr;  // state the tensor maps were encoded for
+    std::vector<CUtensorMap> tmaps;    // per group
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
         if (d_tables) cudaFree(d_tables);
@@ -90,7 +96,9 @@ struct z2_ctx {
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
+    int variant = 0;  // 0 = automatic, 1 = direct loads only, 2 = TMA only where possible
     uint64_t launches = 0;
+    int *d_err = nullptr;  // device flag: a bounded wait gave up
 };
 
 namespace z2 {
@@ -121,17 +129,25 @@ int cuda_fail(z2_ctx *ctx, cudaError_t e, const char *where) {
 int tile_limit(bool c128) { return c128 ? 13 : 14; }
 int regbits(bool c128) { return c128 ? 4 : 5; }
 
+bool tma_possible(bool c128, int tb, int variant) { return variant != 1 && tb <= tma_tile_limit(c128); }
+
 // Choose the tile size and split the qubits into groups (see file comment).
-bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &err) {
+// A strided group of k qubits has a tile of 2^c contiguous x 2^k strided
+// amplitudes, c = tb - k, with 3 <= c (>= 64-byte runs), c <= tb - R (the
+// register bits of the global layout lie in the strided part) and c <= 8 (7
+// for complex128; one TMA box row is at most 256 elements).
+bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err) {
     g = Geometry{};
     g.n = n;
     g.c128 = c128;
     const int R = regbits(c128);
+    constexpr int CMIN = 3;
+    const int CMAX = c128 ? 7 : 8;
     if (n < 8) {
         err = "states of fewer than 8 qubits are not supported";
         return false;
     }
-    if (n <= tile_limit(c128)) {
+    if (n <= tile_limit(c128) && (!tb_override || tb_override >= n)) {
         g.tb = n;
         Group gr;
         gr.lo = 0;
@@ -143,8 +159,10 @@ bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &
         g.order = {0};
         return true;
     }
-    constexpr int CMIN = 3;  // >= 2^3 contiguous amplitudes per strided segment
+    auto kmin = [&](int tb) { return std::max(R, tb - CMAX); };
+    auto kmax = [&](int tb) { return tb - CMIN; };
     int best_tb = 0, best_h = 1 << 30;
+    bool best_tma = false;
     std::vector<int> cands;
     if (tb_override)
         cands.push_back(tb_override);
@@ -153,10 +171,13 @@ bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &
     for (int tb : cands) {
         if (tb < 8 || tb > tile_limit(c128) || tb >= n) continue;
         const int rem = n - tb;
-        const int h = (rem + (tb - CMIN) - 1) / (tb - CMIN);
-        if (h < best_h) {
+        const int h = (rem + kmax(tb) - 1) / kmax(tb);
+        const bool tma = tma_possible(c128, tb, variant);
+        if (variant == 2 && !tma && !tb_override) continue;
+        if (h < best_h || (h == best_h && tma && !best_tma)) {
             best_h = h;
             best_tb = tb;
+            best_tma = tma;
         }
     }
     if (!best_tb) {
@@ -165,9 +186,9 @@ bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &
     }
     const int tb = best_tb, h = best_h;
     int n_low = tb, rem = n - tb;
-    if (rem < R * h) {  // only for h == 1: keep every high group >= R bits
-        n_low = n - R * h;
-        rem = R * h;
+    if (rem < kmin(tb) * h) {  // keep every strided group >= kmin bits
+        n_low = n - kmin(tb) * h;
+        rem = kmin(tb) * h;
     }
     g.tb = tb;
     Group low;
@@ -186,7 +207,7 @@ bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &
         gr.c = tb - k;
         gr.b = lo;
         gr.rot = ((1u << k) - 1u) << gr.c;
-        if (gr.c < CMIN || gr.c > tb - R || gr.b < gr.c) {
+        if (gr.c < CMIN || gr.c > tb - R || gr.c > CMAX || gr.b < gr.c || gr.hi > n) {
             err = "internal tile planning error";
             return false;
         }
@@ -203,6 +224,47 @@ bool plan_geometry(int n, bool c128, int tb_override, Geometry &g, std::string &
         g.order = {0, 1};
     }
     return true;
+}
+
+// 5-D TMA view of the state for one group: (x_lo, tile_lo, x_hi1, x_hi2,
+// tile_hi), with box (2^c', 1, 2^k1, 2^k2, 1) = exactly one tile.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_tensor_map(CUtensorMap *m, void *state, int n, int tb, const Group &gr, bool c128, int &lo_bits) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    int cp = gr.c, bp = gr.b;
+    if (cp > 8) {  // contiguous tile: view it as 2^8 x 2^(tb-8)
+        cp = 8;
+        bp = 8;
+    }
+    const int k = tb - cp, k1 = std::min(k, 8), k2 = k - k1;
+    const int gap = bp - cp, top = n - bp - k;
+    const uint64_t E = c128 ? 16 : 8;
+    const uint32_t inner = c128 ? 2u : 1u;  // FLOAT64 elements per amplitude
+    cuuint64_t dims[5] = {(cuuint64_t(1) << cp) * inner, cuuint64_t(1) << gap, cuuint64_t(1) << k1,
+                          cuuint64_t(1) << k2, cuuint64_t(1) << top};
+    cuuint64_t strides[4] = {(cuuint64_t(1) << cp) * E, (cuuint64_t(1) << bp) * E, (cuuint64_t(1) << (bp + k1)) * E,
+                             (cuuint64_t(1) << (bp + k)) * E};
+    cuuint32_t box[5] = {(cuuint32_t(1) << cp) * inner, 1, cuuint32_t(1) << k1, cuuint32_t(1) << k2, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    lo_bits = gap;
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, state, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 PassArgs make_args(const Lattice &lat, const Geometry &g, const Group &gr) {
@@ -323,6 +385,7 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     }
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
     for (auto &a : P.args) a.p0 = P.gate;
+    P.tma = tma_possible(c128, P.geo.tb, ctx->variant) && encode_fn() != nullptr;
     return Z2_OK;
 }
 
@@ -344,7 +407,7 @@ double theta_at(const z2_run_params &p, int k, int j0, int j1) {
 // Build the plan of steps j0+1 .. j1 (an empty plan when j0 == j1).
 int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, int j0, int j1, Plan &P) {
     std::string err;
-    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ctx->tb_override, P.geo, err))
+    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ctx->tb_override, ctx->variant, P.geo, err))
         return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_RX_TAN;
     if (j1 == j0) return upload_plan(ctx, lat, P);
@@ -381,24 +444,64 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
     const auto &g = P.geo;
     const bool c128 = g.c128;
     const uint64_t ntiles = 1ull << (g.n - g.tb);
-    const int grid = (int)std::min<uint64_t>(ntiles, 1u << 20);
     const size_t step_bytes = sizeof(PassStepHost);
-    if (g.groups.size() == 1 && !P.passes.empty()) {
-        // single tile: the whole pass list in one launch, state held in registers
-        Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[0], P.d_steps, (int)P.passes.size(),
-                                       P.d_tables, grid, st));
-        ctx->launches += 1;
-    } else {
-        for (size_t i = 0; i < P.passes.size(); ++i) {
-            const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
-            Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[P.passes[i].group], sp, 1, P.d_tables,
-                                           grid, st));
+    const bool single = g.groups.size() == 1;
+    if (P.tma && !P.passes.empty()) {
+        if (P.tmap_state != state || P.tmaps.size() != g.groups.size()) {
+            P.tmaps.assign(g.groups.size(), CUtensorMap{});
+            for (size_t i = 0; i < g.groups.size(); ++i) {
+                int lo_bits = 0;
+                if (!make_tensor_map(&P.tmaps[i], state, g.n, g.tb, g.groups[i], c128, lo_bits))
+                    return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                P.args[i].tma_lo_bits = lo_bits;
+            }
+            P.tmap_state = state;
         }
-        ctx->launches += P.passes.size();
+        const int smem = tma_smem_bytes(c128, g.tb);
+        const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1024)));
+        const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->sm_count * per_sm);
+        if (single) {
+            Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[0], &P.tmaps[0], P.d_steps, (int)P.passes.size(),
+                                         P.d_tables, ctx->d_err, grid, st));
+            ctx->launches += 1;
+        } else {
+            for (size_t i = 0; i < P.passes.size(); ++i) {
+                const int gi = P.passes[i].group;
+                const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+                Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[gi], &P.tmaps[gi], sp, 1, P.d_tables,
+                                             ctx->d_err, grid, st));
+            }
+            ctx->launches += P.passes.size();
+        }
+    } else if (!P.passes.empty()) {
+        const int grid = (int)std::min<uint64_t>(ntiles, 1u << 20);
+        if (single) {
+            // single tile: the whole pass list in one launch, state held in registers
+            Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[0], P.d_steps, (int)P.passes.size(),
+                                           P.d_tables, grid, st));
+            ctx->launches += 1;
+        } else {
+            for (size_t i = 0; i < P.passes.size(); ++i) {
+                const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+                Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[P.passes[i].group], sp, 1,
+                                               P.d_tables, grid, st));
+            }
+            ctx->launches += P.passes.size();
+        }
     }
     if (P.flip) {
         Z2_CUDA(ctx, launch_flip_all(c128, state, g.n, ctx->sm_count * 8, st));
         ctx->launches += 1;
+    }
+    return Z2_OK;
+}
+
+int check_device_error(z2_ctx *ctx) {
+    int flag = 0;
+    Z2_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return fail(ctx, Z2_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up; results are invalid");
     }
     return Z2_OK;
 }
@@ -435,7 +538,7 @@ Plan *get_plan(z2_ctx *ctx, const std::string &key) {
 // Hadamard layer plan: every group once, scale 2^{-k/2} per group pass.
 int build_hadamard_plan(z2_ctx *ctx, const Lattice &lat, bool c128, Plan &P) {
     std::string err;
-    if (!plan_geometry(lat.n_links, c128, ctx->tb_override, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+    if (!plan_geometry(lat.n_links, c128, ctx->tb_override, ctx->variant, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_HADAMARD;
     for (int gi = 0; gi < (int)P.geo.groups.size(); ++gi) {
         HostPass hp{};
@@ -491,7 +594,14 @@ int z2_ctx_create(int device, z2_ctx **out) {
         if (ctx->d_out) cudaFree(ctx->d_out);
         return fail(nullptr, Z2_ERR_OOM, "context scratch allocation failed");
     }
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->d_partials);
+        cudaFree(ctx->d_out);
+        cudaFreeHost(ctx->h_out);
+        return fail(nullptr, Z2_ERR_OOM, "context scratch allocation failed");
+    }
     if (const char *s = std::getenv("Z2_TILE_BITS")) ctx->tb_override = std::atoi(s);
+    if (const char *s = std::getenv("Z2_PASS_VARIANT")) ctx->variant = std::string(s) == "direct" ? 1 : (std::string(s) == "tma" ? 2 : 0);
     *out = ctx.release();
     return Z2_OK;
 }
@@ -503,6 +613,7 @@ int z2_ctx_destroy(z2_ctx *ctx) {
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->d_out) cudaFree(ctx->d_out);
     if (ctx->h_out) cudaFreeHost(ctx->h_out);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
     return Z2_OK;
 }
@@ -515,6 +626,22 @@ int z2_ctx_launch_count(const z2_ctx *ctx, uint64_t *out) {
 
 int z2_ctx_flush_plans(z2_ctx *ctx) {
     if (!ctx) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    Z2_CUDA(ctx, cudaDeviceSynchronize());
+    ctx->plans.clear();
+    return Z2_OK;
+}
+
+int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
+    if (!ctx) return fail(nullptr, Z2_ERR_ARG, "NULL argument");
+    if (option == Z2_OPT_TILE_BITS) {
+        if (value != 0 && (value < 8 || value > 14)) return fail(ctx, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
+        ctx->tb_override = value;
+    } else if (option == Z2_OPT_PASS_VARIANT) {
+        if (value < 0 || value > 2) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0, 1 or 2");
+        ctx->variant = value;
+    } else {
+        return fail(ctx, Z2_ERR_ARG, "unknown option");
+    }
     Z2_CUDA(ctx, cudaDeviceSynchronize());
     ctx->plans.clear();
     return Z2_OK;
@@ -626,7 +753,7 @@ int z2_apply_plaquettes(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, v
     const std::string key = plan_key("plaq", lat->lat, &pp, 0, 0, theta);
     if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
             std::string err;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, Q.geo, err))
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, ctx->variant, Q.geo, err))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             push_table(Q, lat->lat, theta, {1, 0});
@@ -653,7 +780,7 @@ int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
     const std::string key = plan_key("rx", lat->lat, &pp, 0, 0, dt);
     if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
             std::string err;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, Q.geo, err))
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, ctx->variant, Q.geo, err))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             const GateSplit gs = split_gate(dt);
@@ -770,6 +897,7 @@ int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void 
     if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
     Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, (off_fid + 4) * sizeof(double), cudaMemcpyDeviceToHost, st));
     Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    if (int rc = check_device_error(ctx)) return rc;
     const double *h = ctx->h_out;
     std::memset(out, 0, sizeof(*out));
     const double nan = std::nan("");

@@ -258,3 +258,28 @@ def test_argument_errors(ctx):
     z2.z2_init_plus(ctx, lat.handle, z2.Z2_C64, g)
     z2.z2_evolve(ctx, lat.handle, z2.params(1, 1, 10), g, 4, 4)
     assert np.allclose(host(g), 2 ** -9)
+
+
+@pytest.mark.parametrize("variant,tile_bits", [(1, 0), (2, 0), (2, 12), (1, 13), (2, 11), (1, 10)])
+@pytest.mark.parametrize("d,L", [(2, (3, 3)), (2, (5, 2)), (2, (4, 3)), (3, (2, 2, 2))])
+def test_kernel_variants_and_tilings(ctx, variant, tile_bits, d, L):
+    # every execution variant (direct global loads / TMA pipeline) and tile
+    # size gives the same evolution as the oracle
+    lat = z2.Lattice(d, L)
+    ol = OLattice(d, L)
+    lam, T, M = 2.2, 1.2, 9
+    psi = oracle.run(ol, lam, T, M, 1)
+    z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, variant)
+    z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, tile_bits)
+    try:
+        for precision in PRECS:
+            g = torch.empty(1 << ol.n_links, dtype=torch.complex128 if precision else torch.complex64, device="cuda")
+            z2.z2_init_plus(ctx, lat.handle, precision, g)
+            z2.z2_evolve(ctx, lat.handle, z2.params(lam, T, M, 1, precision), g, 0, M)
+            assert rel_err(host(g), psi) < (1e-11 if precision else 1e-5), (variant, tile_bits, precision)
+            info = z2.z2_evolve_plan_info(ctx, lat.handle, z2.params(lam, T, M, 1, precision), 0, M)
+            if tile_bits and tile_bits < ol.n_links and not (precision and tile_bits > 13):
+                assert info.tile_bits == tile_bits
+    finally:
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 0)
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 0)
