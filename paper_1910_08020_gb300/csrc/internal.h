@@ -68,8 +68,10 @@ struct PassArgs {
 // Launchers (kernels.cu).  All return the cudaError_t of the launch.
 // `steps` is a device array of PassStep (pass_kernel.cuh), `tables` a device
 // array of phase tables, (Z2_MAX_PLAQ + 1) amplitudes of the state's type each.
+// fmt (complex64 only): bit 0 = the input is in the split-pair format,
+// bit 1 = write the split-pair format (see pass_packed.cuh).
 cudaError_t launch_pass_steps(bool c128, int tb, int op, void *psi, const PassArgs &a, const void *steps,
-                              int n_steps, const void *tables, int grid, cudaStream_t st);
+                              int n_steps, const void *tables, int fmt, int grid, cudaStream_t st);
 int pass_threads(bool c128, int tb);
 // TMA-pipelined persistent variant: `tmap` is a CUtensorMap (5-D view of the
 // state, see make_tensor_map in runtime.cpp); `err` a device flag set to 1 if

@@ -11,14 +11,14 @@ static_assert(sizeof(z2::PassStep) == sizeof(z2::PassStepHost), "pass step layou
 namespace z2 {
 
 cudaError_t launch_pass_c64(int tb, int op, void *psi, const PassArgs &a, const void *steps, int n_steps,
-                            const void *tables, int grid, cudaStream_t st);
+                            const void *tables, int fmt, int grid, cudaStream_t st);
 cudaError_t launch_pass_c128(int tb, int op, void *psi, const PassArgs &a, const void *steps, int n_steps,
-                             const void *tables, int grid, cudaStream_t st);
+                             const void *tables, int fmt, int grid, cudaStream_t st);
 
 cudaError_t launch_pass_steps(bool c128, int tb, int op, void *psi, const PassArgs &a, const void *steps,
-                              int n_steps, const void *tables, int grid, cudaStream_t st) {
-    return c128 ? launch_pass_c128(tb, op, psi, a, steps, n_steps, tables, grid, st)
-                : launch_pass_c64(tb, op, psi, a, steps, n_steps, tables, grid, st);
+                              int n_steps, const void *tables, int fmt, int grid, cudaStream_t st) {
+    return c128 ? launch_pass_c128(tb, op, psi, a, steps, n_steps, tables, fmt, grid, st)
+                : launch_pass_c64(tb, op, psi, a, steps, n_steps, tables, fmt, grid, st);
 }
 
 cudaError_t launch_pass_tma_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps, int n_steps,

@@ -34,7 +34,8 @@ static cudaError_t launch_op(int tb, double2 *psi, const PassArgs &a, const Pass
 }
 
 cudaError_t launch_pass_c128(int tb, int op, void *psi, const PassArgs &a, const void *steps, int n_steps,
-                               const void *tables, int grid, cudaStream_t st) {
+                               const void *tables, int fmt, int grid, cudaStream_t st) {
+    (void)fmt;  // complex128 passes always use the interleaved format
     auto ps = static_cast<const PassStep *>(steps);
     auto p = static_cast<double2 *>(psi);
     auto tab = static_cast<const double2 *>(tables);

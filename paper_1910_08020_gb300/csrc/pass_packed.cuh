@@ -1,0 +1,338 @@
+// Packed-pair fused pass for complex64 states (Blackwell f32x2 arithmetic).
+//
+// Same operation as pass_kernel (rot1 -> plaquette table | scale -> rot2 on a
+// tile of 2^TB amplitudes, see there), organised for half the instructions:
+//
+//   * amplitudes x and x^1 (tile bit 0 = global bit 0) always travel together
+//     as a "pair" held in two 64-bit registers, re = (re_x, re_x^1) and
+//     im = (im_x, im_x^1); every butterfly on any other bit then updates two
+//     amplitudes per packed instruction (fma.rn.f32x2 / add / sub / mul), the
+//     transverse-field butterfly (a, b) -> (a + i t b, b + i t a) costing one
+//     f32x2 FMA per amplitude;
+//   * a thread holds 2^W pairs; register layout q keeps the pair-index bits
+//     [w0(q), w0(q) + W) in registers, the remaining pair-index bits name the
+//     thread; changing layout moves 16-byte pairs through shared memory, one
+//     padding slot every 2^W pairs (conflict-free for every layout and size);
+//   * between the passes of one evolution the state is stored "split": each
+//     16-byte pair as (re_x, re_x^1, im_x, im_x^1), so loads and stores need
+//     no register shuffles; the first and last pass convert from and to the
+//     interleaved (re, im) format of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace z2 {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int TB, int W>
+struct PTile {
+    static constexpr int Y = TB - 1;              // pair-index bits
+    static constexpr int NP = 1 << W;             // pairs per thread
+    static constexpr int NT = 1 << (Y - W);       // threads per CTA
+    static constexpr int K = (Y + W - 1) / W;     // register layouts
+    static constexpr int SLOTS = (1 << Y) + (1 << (Y - W));
+    static constexpr int NTW = NT < 32 ? 32 : NT;
+    static constexpr int MINB = (512 / NTW) < 1 ? 1 : (512 / NTW);
+    __host__ __device__ static constexpr int w0(int q) { return Y - W * (q + 1) > 0 ? Y - W * (q + 1) : 0; }
+    // pair-index bits rotated while in layout q
+    __host__ __device__ static constexpr uint32_t ownY(int q) {
+        return q == K - 1 ? ((1u << (Y - q * W)) - 1u) : (((1u << W) - 1u) << w0(q));
+    }
+    __device__ static __forceinline__ uint32_t base(int q, uint32_t t) {
+        const int r = w0(q);
+        return (t & ((1u << r) - 1u)) | ((t >> r) << (r + W));
+    }
+    __host__ __device__ static constexpr uint32_t slot(uint32_t y) { return y + (y >> W); }
+};
+
+template <int OP>
+__device__ __forceinline__ void bfly2(u64 &ra, u64 &ia, u64 &rb, u64 &ib, u64 tt, u64 mt) {
+    if (OP == OP_RX_TAN) {
+        const u64 nra = fma2(mt, ib, ra), nia = fma2(tt, rb, ia);
+        const u64 nrb = fma2(mt, ia, rb), nib = fma2(tt, ra, ib);
+        ra = nra;
+        ia = nia;
+        rb = nrb;
+        ib = nib;
+    } else {
+        const u64 nra = add2(ra, rb), nrb = sub2(ra, rb);
+        const u64 nia = add2(ia, ib), nib = sub2(ia, ib);
+        ra = nra;
+        rb = nrb;
+        ia = nia;
+        ib = nib;
+    }
+}
+
+// the gate on tile bit 0: between the two halves of every pair
+template <int OP>
+__device__ __forceinline__ void bfly_in_pair(u64 &re, u64 &im, float t) {
+    float ra, rb, ia, ib;
+    upk2(re, ra, rb);
+    upk2(im, ia, ib);
+    if (OP == OP_RX_TAN) {
+        re = pk2(fmaf(-t, ib, ra), fmaf(-t, ia, rb));
+        im = pk2(fmaf(t, rb, ia), fmaf(t, ra, ib));
+    } else {
+        re = pk2(ra + rb, ra - rb);
+        im = pk2(ia + ib, ia - ib);
+    }
+}
+
+template <int TB, int W, int Q, int OP>
+__device__ __forceinline__ void prot(u64 (&re)[1 << W], u64 (&im)[1 << W], uint32_t mask, float t) {
+    using T = PTile<TB, W>;
+    const u64 tt = pk2(t, t), mt = pk2(-t, -t);
+    if (Q == 0 && (mask & 1u)) {
+#pragma unroll
+        for (int j = 0; j < T::NP; ++j) bfly_in_pair<OP>(re[j], im[j], t);
+    }
+    const uint32_t m = ((mask >> 1) & T::ownY(Q)) >> T::w0(Q);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        if (m & (1u << q)) {
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j)
+                if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tt, mt);
+        }
+    }
+}
+
+template <int TB, int W, int QA, int QB>
+__device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm, uint32_t t) {
+    using T = PTile<TB, W>;
+    ulonglong2 *sa = sm + T::slot(T::base(QA, t));
+#pragma unroll
+    for (int j = 0; j < T::NP; ++j) sa[T::slot((uint32_t)j << T::w0(QA))] = make_ulonglong2(re[j], im[j]);
+    __syncthreads();
+    const ulonglong2 *sb = sm + T::slot(T::base(QB, t));
+#pragma unroll
+    for (int j = 0; j < T::NP; ++j) {
+        const ulonglong2 v = sb[T::slot((uint32_t)j << T::w0(QB))];
+        re[j] = v.x;
+        im[j] = v.y;
+    }
+}
+
+// plaquette phase table or real scale, in layout Q
+template <int TB, int W, int Q>
+__device__ __forceinline__ void pmid(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassArgs &a, int mid, double scale,
+                                     uint32_t ptile, uint32_t t, const float *tabr, const float *tabi) {
+    using T = PTile<TB, W>;
+    if (mid == MID_SCALE) {
+        const float s = (float)scale;
+        const u64 s2 = pk2(s, s);
+#pragma unroll
+        for (int j = 0; j < T::NP; ++j) {
+            re[j] = mul2(re[j], s2);
+            im[j] = mul2(im[j], s2);
+        }
+    } else if (mid == MID_TABLE) {
+        const int r = T::w0(Q);
+        uint32_t p = ptile;
+#pragma unroll
+        for (int i = 0; i < T::Y - W; ++i) {
+            const int ybit = i < r ? i : i + W;
+            if ((t >> i) & 1u) p ^= a.tcol[ybit + 1];
+        }
+        const uint32_t c0 = a.tcol[0];
+#pragma unroll
+        for (int gi = 0; gi < T::NP; ++gi) {
+            if (gi) p ^= a.tcol[r + ctz_c(gi) + 1];
+            const int j = gi ^ (gi >> 1);
+            const int k0 = __popc(p), k1 = __popc(p ^ c0);
+            const u64 tr = pk2(tabr[k0], tabr[k1]), ti = pk2(tabi[k0], tabi[k1]);
+            const u64 nre = sub2(mul2(re[j], tr), mul2(im[j], ti));
+            const u64 nim = fma2(re[j], ti, mul2(im[j], tr));
+            re[j] = nre;
+            im[j] = nim;
+        }
+    }
+}
+
+template <int TB, int W, int OP>
+__device__ __forceinline__ void prot_in(int q, u64 (&re)[1 << W], u64 (&im)[1 << W], uint32_t mask, float t) {
+    constexpr int K = PTile<TB, W>::K;
+    switch (q) {
+        case 0: prot<TB, W, 0, OP>(re, im, mask, t); break;
+        // tile bit 0 (inside the pairs) belongs to layout 0
+        case 1: prot<TB, W, (1 < K ? 1 : 0), OP>(re, im, mask & ~1u, t); break;
+        case 2: prot<TB, W, (2 < K ? 2 : 0), OP>(re, im, mask & ~1u, t); break;
+        default: prot<TB, W, (3 < K ? 3 : 0), OP>(re, im, mask & ~1u, t); break;
+    }
+}
+
+template <int TB, int W>
+__device__ __forceinline__ void pmid_in(int q, u64 (&re)[1 << W], u64 (&im)[1 << W], const PassArgs &a, int mid,
+                                        double scale, uint32_t ptile, uint32_t t, const float *tabr,
+                                        const float *tabi) {
+    constexpr int K = PTile<TB, W>::K;
+    switch (q) {
+        case 0: pmid<TB, W, 0>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
+        case 1: pmid<TB, W, (1 < K ? 1 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
+        case 2: pmid<TB, W, (2 < K ? 2 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
+        default: pmid<TB, W, (3 < K ? 3 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
+    }
+}
+
+template <int TB, int W, int QA>
+__device__ __forceinline__ void prelayout_from(int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
+                                               uint32_t t) {
+    constexpr int K = PTile<TB, W>::K;
+    switch (qb) {
+        case 0: prelayout<TB, W, QA, 0>(re, im, sm, t); break;
+        case 1: prelayout<TB, W, QA, (1 < K ? 1 : 0)>(re, im, sm, t); break;
+        case 2: prelayout<TB, W, QA, (2 < K ? 2 : 0)>(re, im, sm, t); break;
+        default: prelayout<TB, W, QA, (3 < K ? 3 : 0)>(re, im, sm, t); break;
+    }
+}
+
+template <int TB, int W>
+__device__ __forceinline__ void prelayout_rt(int qa, int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
+                                             uint32_t t) {
+    constexpr int K = PTile<TB, W>::K;
+    switch (qa) {
+        case 0: prelayout_from<TB, W, 0>(qb, re, im, sm, t); break;
+        case 1: prelayout_from<TB, W, (1 < K ? 1 : 0)>(qb, re, im, sm, t); break;
+        case 2: prelayout_from<TB, W, (2 < K ? 2 : 0)>(qb, re, im, sm, t); break;
+        default: prelayout_from<TB, W, (3 < K ? 3 : 0)>(qb, re, im, sm, t); break;
+    }
+}
+
+// fmt bit 0: the input is split-pair, bit 1: write the output split-pair
+template <int TB, int W, int OP>
+__global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
+    pass_kernel_packed(float2 *__restrict__ psi, const __grid_constant__ PassArgs a,
+                       const PassStep *__restrict__ steps, int n_steps, const float2 *__restrict__ tables, int fmt) {
+    using T = PTile<TB, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2 *sm = reinterpret_cast<ulonglong2 *>(smem_raw);
+    __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
+
+    const uint32_t t = threadIdx.x;
+    const float gate = (float)a.p0;
+    const int c = a.c, b = a.b;
+    const int hib = b + TB - c;
+    const uint64_t ntiles = 1ull << (a.n - TB);
+    // global index of the thread's first pair (tile index 2t) and the register stride
+    const uint32_t x0 = 2u * t;
+    const uint64_t gthr = (uint64_t)(x0 & ((1u << c) - 1u)) | ((uint64_t)(c < TB ? (x0 >> c) : 0u) << b);
+    const int rbit = 1 + T::w0(0);  // tile bit of register bit 0 in layout 0
+    const int sj = (c == TB) ? rbit : (b + rbit - c);
+    const uint64_t stride = 1ull << sj;
+    const bool in_split = fmt & 1, out_split = fmt & 2;
+
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
+        const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
+
+        u64 re[T::NP], im[T::NP];
+        {
+            const float2 *p = psi + g0 + gthr;
+            if (in_split) {
+#pragma unroll
+                for (int j = 0; j < T::NP; ++j, p += stride) {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+                    re[j] = v.x;
+                    im[j] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < T::NP; ++j, p += stride) {
+                    const float4 v = *reinterpret_cast<const float4 *>(p);
+                    re[j] = pk2(v.x, v.z);
+                    im[j] = pk2(v.y, v.w);
+                }
+            }
+        }
+        for (int s = 0; s < n_steps; ++s) {
+            const PassStep st = steps[s];
+            if (st.mid == MID_TABLE) {
+                __syncthreads();
+                for (uint32_t q = t; q < (uint32_t)a.np1; q += T::NT) {
+                    const float2 e = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
+                    tabr[q] = e.x;
+                    tabi[q] = e.y;
+                }
+                __syncthreads();
+            }
+            int cur = 0;
+            prot_in<TB, W, OP>(0, re, im, st.rot1, gate);
+#pragma unroll
+            for (int q = 1; q < T::K; ++q) {
+                if ((st.rot1 >> 1) & T::ownY(q)) {
+                    prelayout_rt<TB, W>(cur, q, re, im, sm, t);
+                    cur = q;
+                    prot_in<TB, W, OP>(q, re, im, st.rot1, gate);
+                }
+            }
+            pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
+            prot_in<TB, W, OP>(cur, re, im, cur == 0 ? st.rot2 : (st.rot2 & ~1u), gate);
+            const int first = cur;
+#pragma unroll
+            for (int q = T::K - 1; q >= 1; --q) {
+                if (q != first && ((st.rot2 >> 1) & T::ownY(q))) {
+                    prelayout_rt<TB, W>(cur, q, re, im, sm, t);
+                    cur = q;
+                    prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, gate);
+                }
+            }
+            if (cur != 0) {
+                prelayout_rt<TB, W>(cur, 0, re, im, sm, t);
+                if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, gate);
+            }
+        }
+        uint64_t off = g0 + gthr;
+        asm volatile("" : "+l"(off));
+        float2 *p = psi + off;
+        if (out_split) {
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j, p += stride)
+                *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(re[j], im[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j, p += stride) {
+                float r0, r1, i0, i1;
+                upk2(re[j], r0, r1);
+                upk2(im[j], i0, i1);
+                *reinterpret_cast<float4 *>(p) = make_float4(r0, i0, r1, i1);
+            }
+        }
+    }
+}
+
+}  // namespace z2

@@ -246,9 +246,10 @@ bool make_tensor_map(CUtensorMap *m, void *state, int n, int tb, const Group &gr
     auto enc = encode_fn();
     if (!enc) return false;
     int cp = gr.c, bp = gr.b;
-    if (cp > 8) {  // contiguous tile: view it as 2^8 x 2^(tb-8)
-        cp = 8;
-        bp = 8;
+    const int cmax = c128 ? 7 : 8;  // a box row holds at most 256 FLOAT64 elements
+    if (cp > cmax) {                // contiguous tile: view it as 2^cmax x 2^(tb-cmax)
+        cp = cmax;
+        bp = cmax;
     }
     const int k = tb - cp, k1 = std::min(k, 8), k2 = k - k1;
     const int gap = bp - cp, top = n - bp - k;
@@ -478,13 +479,17 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
         if (single) {
             // single tile: the whole pass list in one launch, state held in registers
             Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[0], P.d_steps, (int)P.passes.size(),
-                                           P.d_tables, grid, st));
+                                           P.d_tables, 0, grid, st));
             ctx->launches += 1;
         } else {
+            // complex64: the passes in between keep the state in the split-pair
+            // format; the first converts from, the last back to, (re, im) pairs
+            const size_t last = P.passes.size() - 1;
             for (size_t i = 0; i < P.passes.size(); ++i) {
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+                const int fmt = c128 ? 0 : ((i > 0 ? 1 : 0) | (i < last ? 2 : 0));
                 Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[P.passes[i].group], sp, 1,
-                                               P.d_tables, grid, st));
+                                               P.d_tables, fmt, grid, st));
             }
             ctx->launches += P.passes.size();
         }
