@@ -161,6 +161,8 @@ def main():
     ap.add_argument("--workload", default="4x4", choices=sorted(WORKLOADS))
     ap.add_argument("--decomp", default="sym", choices=["sym", "first"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA")
+    ap.add_argument("--tile-bits", type=int, default=0)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     decomp = 1 if args.decomp == "sym" else 0
@@ -182,6 +184,10 @@ def main():
         dist = dist_mod
     z2.load()
     ctx = z2.Context(local)
+    if args.variant:
+        z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_PASS_VARIANT, args.variant)
+    if args.tile_bits:
+        z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_TILE_BITS, args.tile_bits)
     lat = z2.Lattice(wl["d"], wl["L"])
     n = lat.n_links
     p = z2.params(wl["lam"], wl["T"], wl["M"], decomp, z2.Z2_C64)
@@ -270,7 +276,8 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "fidelity_ref": "device-resident reference state (|+>^N)"},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": f"pass_kernel<float2,{info.tile_bits},RX>",
+            "roofline": {"bound": "hbm", "kernel": f"pass_kernel_packed<{info.tile_bits},4,RX>" if args.variant != 2
+                         else f"pass_kernel_tma<float2,{info.tile_bits},RX>",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": None,
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},

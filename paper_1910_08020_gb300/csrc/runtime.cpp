@@ -129,7 +129,8 @@ int cuda_fail(z2_ctx *ctx, cudaError_t e, const char *where) {
 int tile_limit(bool c128) { return c128 ? 13 : 14; }
 int regbits(bool c128) { return c128 ? 4 : 5; }
 
-bool tma_possible(bool c128, int tb, int variant) { return variant != 1 && tb <= tma_tile_limit(c128); }
+// the TMA-pipelined variant is used on request only (it holds one CTA per SM)
+bool tma_possible(bool c128, int tb, int variant) { return variant == 2 && tb <= tma_tile_limit(c128); }
 
 // Choose the tile size and split the qubits into groups (see file comment).
 // A strided group of k qubits has a tile of 2^c contiguous x 2^k strided
