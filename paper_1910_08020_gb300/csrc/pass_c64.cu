@@ -50,6 +50,49 @@ cudaError_t launch_pass_c64(int tb, int op, void *psi, const PassArgs &a, const 
 
 int packed_threads(int tb) { return 1 << (tb - 1 - PACK_W); }
 
+template <int TB, int OP>
+static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps,
+                                  const float2 *tables, int fmt, int *err, int grid, cudaStream_t st) {
+    using T = PTile<TB, PACK_W>;
+    using RT = RingTile<TB, PACK_W>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    pass_kernel_ring<TB, PACK_W, OP><<<grid, 2 * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
+    return cudaGetLastError();
+}
+
+template <int OP>
+static cudaError_t launch_ring_op(int tb, const PassArgs &a, const CUtensorMap &m, const PassStep *steps,
+                                  const float2 *tables, int fmt, int *err, int grid, cudaStream_t st) {
+    switch (tb) {
+        case 10: return launch_ring_tb<10, OP>(a, m, steps, tables, fmt, err, grid, st);
+        case 11: return launch_ring_tb<11, OP>(a, m, steps, tables, fmt, err, grid, st);
+        case 12: return launch_ring_tb<12, OP>(a, m, steps, tables, fmt, err, grid, st);
+        case 13: return launch_ring_tb<13, OP>(a, m, steps, tables, fmt, err, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
+                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st) {
+    auto ps = static_cast<const PassStep *>(steps);
+    auto tab = static_cast<const float2 *>(tables);
+    const CUtensorMap &m = *static_cast<const CUtensorMap *>(tmap);
+    return op == OP_HADAMARD ? launch_ring_op<OP_HADAMARD>(tb, a, m, ps, tab, fmt, err, grid, st)
+                             : launch_ring_op<OP_RX_TAN>(tb, a, m, ps, tab, fmt, err, grid, st);
+}
+
+int ring_tile_limits(int *lo, int *hi) {
+    *lo = 10;
+    *hi = 13;
+    return 0;
+}
+
 template <typename C, int TB, int OP>
 static cudaError_t launch_tma_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps, int n_steps,
                                  const C *tables, int *err, int grid, cudaStream_t st) {

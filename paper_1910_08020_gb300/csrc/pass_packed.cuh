@@ -130,13 +130,24 @@ __device__ __forceinline__ void prot(u64 (&re)[1 << W], u64 (&im)[1 << W], uint3
     }
 }
 
+// barrier over the threads that share one tile: the whole CTA (bar < 0) or
+// named barrier `bar` of NT threads (two tiles per CTA)
+template <int NT>
+__device__ __forceinline__ void tile_sync(int bar) {
+    if (bar < 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
+}
+
 template <int TB, int W, int QA, int QB>
-__device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm, uint32_t t) {
+__device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm, uint32_t t,
+                                          int bar = -1) {
     using T = PTile<TB, W>;
     ulonglong2 *sa = sm + T::slot(T::base(QA, t));
 #pragma unroll
     for (int j = 0; j < T::NP; ++j) sa[T::slot((uint32_t)j << T::w0(QA))] = make_ulonglong2(re[j], im[j]);
-    __syncthreads();
+    tile_sync<T::NT>(bar);
     const ulonglong2 *sb = sm + T::slot(T::base(QB, t));
 #pragma unroll
     for (int j = 0; j < T::NP; ++j) {
@@ -209,25 +220,58 @@ __device__ __forceinline__ void pmid_in(int q, u64 (&re)[1 << W], u64 (&im)[1 <<
 
 template <int TB, int W, int QA>
 __device__ __forceinline__ void prelayout_from(int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
-                                               uint32_t t) {
+                                               uint32_t t, int bar) {
     constexpr int K = PTile<TB, W>::K;
     switch (qb) {
-        case 0: prelayout<TB, W, QA, 0>(re, im, sm, t); break;
-        case 1: prelayout<TB, W, QA, (1 < K ? 1 : 0)>(re, im, sm, t); break;
-        case 2: prelayout<TB, W, QA, (2 < K ? 2 : 0)>(re, im, sm, t); break;
-        default: prelayout<TB, W, QA, (3 < K ? 3 : 0)>(re, im, sm, t); break;
+        case 0: prelayout<TB, W, QA, 0>(re, im, sm, t, bar); break;
+        case 1: prelayout<TB, W, QA, (1 < K ? 1 : 0)>(re, im, sm, t, bar); break;
+        case 2: prelayout<TB, W, QA, (2 < K ? 2 : 0)>(re, im, sm, t, bar); break;
+        default: prelayout<TB, W, QA, (3 < K ? 3 : 0)>(re, im, sm, t, bar); break;
     }
 }
 
 template <int TB, int W>
 __device__ __forceinline__ void prelayout_rt(int qa, int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
-                                             uint32_t t) {
+                                             uint32_t t, int bar = -1) {
     constexpr int K = PTile<TB, W>::K;
     switch (qa) {
-        case 0: prelayout_from<TB, W, 0>(qb, re, im, sm, t); break;
-        case 1: prelayout_from<TB, W, (1 < K ? 1 : 0)>(qb, re, im, sm, t); break;
-        case 2: prelayout_from<TB, W, (2 < K ? 2 : 0)>(qb, re, im, sm, t); break;
-        default: prelayout_from<TB, W, (3 < K ? 3 : 0)>(qb, re, im, sm, t); break;
+        case 0: prelayout_from<TB, W, 0>(qb, re, im, sm, t, bar); break;
+        case 1: prelayout_from<TB, W, (1 < K ? 1 : 0)>(qb, re, im, sm, t, bar); break;
+        case 2: prelayout_from<TB, W, (2 < K ? 2 : 0)>(qb, re, im, sm, t, bar); break;
+        default: prelayout_from<TB, W, (3 < K ? 3 : 0)>(qb, re, im, sm, t, bar); break;
+    }
+}
+
+// one pass step on the registers of a tile (layout 0 in and out)
+template <int TB, int W, int OP>
+__device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, const PassArgs &a,
+                                      float gate, uint32_t ptile, uint32_t t, ulonglong2 *sm, const float *tabr,
+                                      const float *tabi, int bar) {
+    using T = PTile<TB, W>;
+    int cur = 0;
+    prot_in<TB, W, OP>(0, re, im, st.rot1, gate);
+#pragma unroll
+    for (int q = 1; q < T::K; ++q) {
+        if ((st.rot1 >> 1) & T::ownY(q)) {
+            prelayout_rt<TB, W>(cur, q, re, im, sm, t, bar);
+            cur = q;
+            prot_in<TB, W, OP>(q, re, im, st.rot1, gate);
+        }
+    }
+    pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
+    prot_in<TB, W, OP>(cur, re, im, cur == 0 ? st.rot2 : (st.rot2 & ~1u), gate);
+    const int first = cur;
+#pragma unroll
+    for (int q = T::K - 1; q >= 1; --q) {
+        if (q != first && ((st.rot2 >> 1) & T::ownY(q))) {
+            prelayout_rt<TB, W>(cur, q, re, im, sm, t, bar);
+            cur = q;
+            prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, gate);
+        }
+    }
+    if (cur != 0) {
+        prelayout_rt<TB, W>(cur, 0, re, im, sm, t, bar);
+        if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, gate);
     }
 }
 
@@ -290,31 +334,7 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
                 }
                 __syncthreads();
             }
-            int cur = 0;
-            prot_in<TB, W, OP>(0, re, im, st.rot1, gate);
-#pragma unroll
-            for (int q = 1; q < T::K; ++q) {
-                if ((st.rot1 >> 1) & T::ownY(q)) {
-                    prelayout_rt<TB, W>(cur, q, re, im, sm, t);
-                    cur = q;
-                    prot_in<TB, W, OP>(q, re, im, st.rot1, gate);
-                }
-            }
-            pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
-            prot_in<TB, W, OP>(cur, re, im, cur == 0 ? st.rot2 : (st.rot2 & ~1u), gate);
-            const int first = cur;
-#pragma unroll
-            for (int q = T::K - 1; q >= 1; --q) {
-                if (q != first && ((st.rot2 >> 1) & T::ownY(q))) {
-                    prelayout_rt<TB, W>(cur, q, re, im, sm, t);
-                    cur = q;
-                    prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, gate);
-                }
-            }
-            if (cur != 0) {
-                prelayout_rt<TB, W>(cur, 0, re, im, sm, t);
-                if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, gate);
-            }
+            pstep<TB, W, OP>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, -1);
         }
         uint64_t off = g0 + gthr;
         asm volatile("" : "+l"(off));
@@ -333,6 +353,143 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Streaming variant: one CTA per SM made of two independent halves of NT
+// threads, each transforming its own tile with named barriers, fed by a ring
+// of three shared-memory tile buffers that the TMA unit fills ahead of use
+// (cp.async.bulk.tensor + mbarrier) and drains with TMA stores.  Local tile n
+// (global tile blockIdx.x + n * gridDim.x) lives in buffer n % 3 and is worked
+// on by half n % 2; when a half has stored tile n it refills that buffer with
+// tile n + 3, so two tiles are being transformed while the next one streams
+// in.  Multi-tile, single-step passes only (the host launches one per pass).
+// Requires pass_kernel.cuh (TMA and mbarrier helpers) to be included first.
+template <int TB, int W>
+struct RingTile {
+    using T = PTile<TB, W>;
+    static constexpr uint32_t BUF = ((T::SLOTS * 16u + 1023u) / 1024u) * 1024u;
+    static constexpr uint32_t TILE_BYTES = 8u << TB;
+    static constexpr uint32_t SMEM_BYTES = 3 * BUF + 1024;
+};
+
+__device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(bar), "r"(n)
+                 : "memory");
+    return r != 0;
+}
+
+template <int TB, int W, int OP>
+__global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
+    pass_kernel_ring(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
+                     const PassStep *__restrict__ steps, const float2 *__restrict__ tables, int fmt, int *err) {
+    using T = PTile<TB, W>;
+    using RT = RingTile<TB, W>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[3];
+    __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    auto buf = [&](int k) { return reinterpret_cast<ulonglong2 *>(base + k * RT::BUF); };
+
+    const uint32_t half = threadIdx.x / T::NT, t = threadIdx.x % T::NT;
+    const int bar = 1 + (int)half;
+    const float gate = (float)a.p0;
+    const int c = a.c, b = a.b, hib = b + TB - c, lo_bits = a.tma_lo_bits;
+    const bool in_split = fmt & 1, out_split = fmt & 2;
+    const PassStep st = steps[0];
+    const uint64_t ntiles = 1ull << (a.n - TB);
+    const uint64_t nloc = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto gtile = [&](uint64_t n) { return (uint64_t)blockIdx.x + n * gridDim.x; };
+
+    if (st.mid == MID_TABLE)
+        for (uint32_t q = threadIdx.x; q < (uint32_t)a.np1; q += 2 * T::NT) {
+            const float2 e = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
+            tabr[q] = e.x;
+            tabi[q] = e.y;
+        }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(&mbar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (uint64_t n = 0; n < 3 && n < nloc; ++n) {
+            const uint64_t g = gtile(n);
+            mbar_expect_tx(&mbar[n], RT::TILE_BYTES);
+            tma_load_5d(buf((int)n), &tmap, &mbar[n], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
+        }
+
+    for (uint64_t n = half; n < nloc; n += 2) {
+        const int bi = (int)(n % 3);
+        const uint32_t parity = (uint32_t)((n / 3) & 1);
+        bool ok = false;
+        for (uint32_t k = 0; k < MBAR_POLL_LIMIT; ++k)
+            if ((ok = mbar_try_wait(&mbar[bi], parity))) break;
+        if (!bar_and(bar, T::NT, ok)) {
+            if (t == 0) {
+                atomicExch(err, 1);
+                bulk_wait_all();
+            }
+            return;
+        }
+        const uint64_t tile = gtile(n);
+        const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
+        const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
+
+        ulonglong2 *sm = buf(bi);
+        u64 re[T::NP], im[T::NP];
+        // layout 0 from the dense tile image (pair y at slot y)
+        if (in_split) {
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j) {
+                const ulonglong2 v = sm[t | ((uint32_t)j << T::w0(0))];
+                re[j] = v.x;
+                im[j] = v.y;
+            }
+        } else {
+            const float4 *sf = reinterpret_cast<const float4 *>(sm);
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j) {
+                const float4 v = sf[t | ((uint32_t)j << T::w0(0))];
+                re[j] = pk2(v.x, v.z);
+                im[j] = pk2(v.y, v.w);
+            }
+        }
+        tile_sync<T::NT>(bar);  // dense reads done before the padded layouts reuse the buffer
+        pstep<TB, W, OP>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, bar);
+        tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
+        if (out_split) {
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j) sm[t | ((uint32_t)j << T::w0(0))] = make_ulonglong2(re[j], im[j]);
+        } else {
+            float4 *sf = reinterpret_cast<float4 *>(sm);
+#pragma unroll
+            for (int j = 0; j < T::NP; ++j) {
+                float r0, r1, i0, i1;
+                upk2(re[j], r0, r1);
+                upk2(im[j], i0, i1);
+                sf[t | ((uint32_t)j << T::w0(0))] = make_float4(r0, i0, r1, i1);
+            }
+        }
+        fence_proxy_async();
+        tile_sync<T::NT>(bar);
+        if (t == 0) {
+            tma_store_5d(&tmap, sm, (int)(tile & ((1ull << lo_bits) - 1)), (int)(tile >> lo_bits));
+            if (n + 3 < nloc) {
+                bulk_wait_read_all();  // the store has read the buffer
+                const uint64_t g = gtile(n + 3);
+                mbar_expect_tx(&mbar[bi], RT::TILE_BYTES);
+                tma_load_5d(sm, &tmap, &mbar[bi], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
+            }
+        }
+    }
+    if (t == 0) bulk_wait_all();
 }
 
 }  // namespace z2

@@ -76,6 +76,7 @@ struct Plan {
     void *d_tables = nullptr;
     std::vector<PassArgs> args;  // per group
     bool tma = false;                  // TMA-pipelined persistent kernel
+    bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
     const void *tmap_state = nullptr;  // state the tensor maps were encoded for
     std::vector<CUtensorMap> tmaps;    // per group
     ~Plan() {
@@ -96,7 +97,7 @@ struct z2_ctx {
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
-    int variant = 0;  // 0 = automatic, 1 = direct loads only, 2 = TMA only where possible
+    int variant = 0;  // 0 = automatic, 1 = direct loads, 2 = TMA per CTA, 3 = TMA ring (complex64)
     uint64_t launches = 0;
     int *d_err = nullptr;  // device flag: a bounded wait gave up
 };
@@ -388,6 +389,8 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
     for (auto &a : P.args) a.p0 = P.gate;
     P.tma = tma_possible(c128, P.geo.tb, ctx->variant) && encode_fn() != nullptr;
+    P.ring = !c128 && ctx->variant == 3 && P.geo.groups.size() > 1 && P.geo.tb >= 10 && P.geo.tb <= 13 &&
+             encode_fn() != nullptr;
     return Z2_OK;
 }
 
@@ -448,7 +451,7 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
     const uint64_t ntiles = 1ull << (g.n - g.tb);
     const size_t step_bytes = sizeof(PassStepHost);
     const bool single = g.groups.size() == 1;
-    if (P.tma && !P.passes.empty()) {
+    if ((P.tma || P.ring) && !P.passes.empty()) {
         if (P.tmap_state != state || P.tmaps.size() != g.groups.size()) {
             P.tmaps.assign(g.groups.size(), CUtensorMap{});
             for (size_t i = 0; i < g.groups.size(); ++i) {
@@ -458,6 +461,23 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                 P.args[i].tma_lo_bits = lo_bits;
             }
             P.tmap_state = state;
+        }
+        if (P.ring) {
+            const int grid = (int)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)ctx->sm_count);
+            const size_t last = P.passes.size() - 1;
+            for (size_t i = 0; i < P.passes.size(); ++i) {
+                const int gi = P.passes[i].group;
+                const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+                const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
+                Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &P.tmaps[gi], sp, P.d_tables, fmt,
+                                                  ctx->d_err, grid, st));
+            }
+            ctx->launches += P.passes.size();
+            if (P.flip) {
+                Z2_CUDA(ctx, launch_flip_all(c128, state, g.n, ctx->sm_count * 8, st));
+                ctx->launches += 1;
+            }
+            return Z2_OK;
         }
         const int smem = tma_smem_bytes(c128, g.tb);
         const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1024)));
@@ -643,7 +663,7 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
         if (value != 0 && (value < 8 || value > 14)) return fail(ctx, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
         ctx->tb_override = value;
     } else if (option == Z2_OPT_PASS_VARIANT) {
-        if (value < 0 || value > 2) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..3");
         ctx->variant = value;
     } else {
         return fail(ctx, Z2_ERR_ARG, "unknown option");

@@ -260,7 +260,7 @@ def test_argument_errors(ctx):
     assert np.allclose(host(g), 2 ** -9)
 
 
-@pytest.mark.parametrize("variant,tile_bits", [(1, 0), (2, 0), (2, 12), (1, 13), (2, 11), (1, 10)])
+@pytest.mark.parametrize("variant,tile_bits", [(1, 0), (2, 0), (2, 12), (1, 13), (2, 11), (1, 10), (3, 0), (3, 12), (3, 10), (3, 13)])
 @pytest.mark.parametrize("d,L", [(2, (3, 3)), (2, (5, 2)), (2, (4, 3)), (3, (2, 2, 2))])
 def test_kernel_variants_and_tilings(ctx, variant, tile_bits, d, L):
     # every execution variant (direct global loads / TMA pipeline) and tile
