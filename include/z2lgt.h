@@ -227,6 +227,24 @@ int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state
 int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b,
                double *out, void *stream);
 
+/* ---- batched runs: a lambda sweep (many independent adiabatic runs) ------- */
+typedef struct {
+    int32_t d, L[3];      /* lattice                                  */
+    z2_run_params params; /* schedule, decomposition, precision       */
+} z2_run_spec;
+
+#define Z2_SWEEP_PLAIN 0   /* one run after another on one stream, each synchronised            */
+#define Z2_SWEEP_STREAMS 1 /* runs spread over n_streams streams, all enqueued before one wait  */
+#define Z2_SWEEP_GRAPHS 2  /* as STREAMS, each run (|+>, M steps, observables) one CUDA graph   */
+
+/* Runs specs[0 .. n) (each: |+>^N, M steps, observables at s = 1, no
+ * fidelity) and writes out[i]; out[i].status is that run's status.  The
+ * library allocates and frees the device states (n_streams of the largest
+ * size).  Returns Z2_OK if every run succeeded, else the first error.  The
+ * result of a run does not depend on the mode or on the other runs (the same
+ * kernels run on the same data in the same order). */
+int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int32_t n_streams, z2_results *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ __all__ = [
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
     "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap",
-    "Context", "Lattice", "results_dict",
+    "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -73,6 +73,12 @@ class Results(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class RunSpec(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32 * 3), ("params", RunParams)]
+
+
+Z2_SWEEP_PLAIN, Z2_SWEEP_STREAMS, Z2_SWEEP_GRAPHS = 0, 1, 2
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
@@ -101,6 +107,7 @@ _SIGS = {
     "z2_run": [_P, _P, ctypes.POINTER(RunParams), _P, _P, _P, ctypes.POINTER(Results)],
     "z2_zsums": [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
     "z2_overlap": [_P, _I, _I, _P, _P, ctypes.POINTER(_D), _P],
+    "z2_sweep": [_P, ctypes.POINTER(RunSpec), _I, _I, _I, ctypes.POINTER(Results)],
 }
 
 
@@ -269,6 +276,26 @@ def z2_overlap(ctx, n_qubits, precision, a, b, stream=None):
     _check(load().z2_overlap(ctx, n_qubits, precision, _ptr(a), _ptr(b), out.ctypes.data_as(ctypes.POINTER(_D)),
                              _stream(stream)), ctx)
     return complex(out[0], out[1])
+
+
+def run_specs(specs):
+    """List of dicts (d, L, lam, T, M, decomp[, precision, sampling]) -> RunSpec array."""
+    arr = (RunSpec * len(specs))()
+    for i, sp in enumerate(specs):
+        L = list(sp["L"]) + [1] * (3 - len(sp["L"]))
+        arr[i].d = sp["d"]
+        arr[i].L[:] = L[:3]
+        arr[i].params = params(sp["lam"], sp["T"], sp["M"], sp.get("decomp", Z2_SYMMETRIC),
+                               sp.get("precision", Z2_C64), sp.get("sampling", Z2_SAMPLE_STD))
+    return arr
+
+
+def z2_sweep(ctx, specs, mode=Z2_SWEEP_GRAPHS, n_streams=8):
+    """Run a batch of independent adiabatic runs; returns a list of Results."""
+    arr = specs if isinstance(specs, ctypes.Array) else run_specs(specs)
+    out = (Results * len(arr))()
+    _check(load().z2_sweep(ctx, arr, len(arr), int(mode), int(n_streams), out), ctx)
+    return list(out)
 
 
 def results_dict(res, info):

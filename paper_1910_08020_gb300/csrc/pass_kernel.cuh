@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, 1)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ C tab[Z2_MAX_PLAQ + 1];
-    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned start, as an offset into the shared array (keeps the
+    // accesses in the shared address space)
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     auto buf = [&](int k) { return reinterpret_cast<C *>(base + k * TT::BUF_BYTES); };
 
     const uint32_t t = threadIdx.x;

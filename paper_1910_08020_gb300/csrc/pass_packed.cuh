@@ -391,8 +391,9 @@ __global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[3];
     __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
-    unsigned char *base =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned start, as an offset into the shared array (keeps the
+    // accesses in the shared address space)
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     auto buf = [&](int k) { return reinterpret_cast<ulonglong2 *>(base + k * RT::BUF); };
 
     const uint32_t half = threadIdx.x / T::NT, t = threadIdx.x % T::NT;

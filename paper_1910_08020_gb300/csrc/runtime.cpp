@@ -77,8 +77,6 @@ struct Plan {
     std::vector<PassArgs> args;  // per group
     bool tma = false;                  // TMA-pipelined persistent kernel
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
-    const void *tmap_state = nullptr;  // state the tensor maps were encoded for
-    std::vector<CUtensorMap> tmaps;    // per group
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
         if (d_tables) cudaFree(d_tables);
@@ -452,15 +450,14 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
     const size_t step_bytes = sizeof(PassStepHost);
     const bool single = g.groups.size() == 1;
     if ((P.tma || P.ring) && !P.passes.empty()) {
-        if (P.tmap_state != state || P.tmaps.size() != g.groups.size()) {
-            P.tmaps.assign(g.groups.size(), CUtensorMap{});
-            for (size_t i = 0; i < g.groups.size(); ++i) {
-                int lo_bits = 0;
-                if (!make_tensor_map(&P.tmaps[i], state, g.n, g.tb, g.groups[i], c128, lo_bits))
-                    return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-                P.args[i].tma_lo_bits = lo_bits;
-            }
-            P.tmap_state = state;
+        // tensor maps name the state buffer, so they are encoded per call
+        // (a few microseconds) and passed by value to each launch
+        std::vector<CUtensorMap> tmaps(g.groups.size());
+        for (size_t i = 0; i < g.groups.size(); ++i) {
+            int lo_bits = 0;
+            if (!make_tensor_map(&tmaps[i], state, g.n, g.tb, g.groups[i], c128, lo_bits))
+                return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            P.args[i].tma_lo_bits = lo_bits;
         }
         if (P.ring) {
             const int grid = (int)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)ctx->sm_count);
@@ -469,7 +466,7 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                 const int gi = P.passes[i].group;
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
-                Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &P.tmaps[gi], sp, P.d_tables, fmt,
+                Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
                                                   ctx->d_err, grid, st));
             }
             ctx->launches += P.passes.size();
@@ -483,14 +480,14 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
         const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1024)));
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->sm_count * per_sm);
         if (single) {
-            Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[0], &P.tmaps[0], P.d_steps, (int)P.passes.size(),
+            Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[0], &tmaps[0], P.d_steps, (int)P.passes.size(),
                                          P.d_tables, ctx->d_err, grid, st));
             ctx->launches += 1;
         } else {
             for (size_t i = 0; i < P.passes.size(); ++i) {
                 const int gi = P.passes[i].group;
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
-                Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[gi], &P.tmaps[gi], sp, 1, P.d_tables,
+                Z2_CUDA(ctx, launch_pass_tma(c128, g.tb, P.op, P.args[gi], &tmaps[gi], sp, 1, P.d_tables,
                                              ctx->d_err, grid, st));
             }
             ctx->launches += P.passes.size();
@@ -842,12 +839,20 @@ int z2_apply_hadamard(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
     return exec_plan(ctx, *P, state, (cudaStream_t)stream);
 }
 
-static int zsums_device(z2_ctx *ctx, int n, bool c128, const void *state, const uint64_t *masks, int n_masks,
-                        int out_off, cudaStream_t st) {
+struct Scratch {
+    double *d_partials;  // reduction partials (2^16 x 32 doubles for the context's own)
+    double *d_out;       // reduction outputs (OUT_DOUBLES)
+    double *h_out;       // pinned copy of d_out
+};
+
+static Scratch ctx_scratch(z2_ctx *ctx) { return Scratch{ctx->d_partials, ctx->d_out, ctx->h_out}; }
+
+static int zsums_device(z2_ctx *ctx, const Scratch &sc, int n, bool c128, const void *state, const uint64_t *masks,
+                        int n_masks, int out_off, cudaStream_t st) {
     const int chunk = max_zsum_masks();
     for (int k = 0; k < n_masks; k += chunk) {
         const int m = std::min(chunk, n_masks - k);
-        Z2_CUDA(ctx, launch_zsums(c128, state, n, masks + k, m, ctx->d_partials, ctx->d_out + out_off + k, st));
+        Z2_CUDA(ctx, launch_zsums(c128, state, n, masks + k, m, sc.d_partials, sc.d_out + out_off + k, st));
         ctx->launches += 2;
     }
     return Z2_OK;
@@ -861,7 +866,8 @@ int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state
     if (n_masks < 0 || n_masks > OUT_DOUBLES) return fail(ctx, Z2_ERR_ARG, "need 0 <= n_masks <= 256");
     if (int rc = check_state(ctx, state)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (int rc = zsums_device(ctx, n_qubits, precision == Z2_C128, state, masks, n_masks, 0, st)) return rc;
+    if (int rc = zsums_device(ctx, ctx_scratch(ctx), n_qubits, precision == Z2_C128, state, masks, n_masks, 0, st))
+        return rc;
     Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, n_masks * sizeof(double), cudaMemcpyDeviceToHost, st));
     Z2_CUDA(ctx, cudaStreamSynchronize(st));
     std::memcpy(out, ctx->h_out, n_masks * sizeof(double));
@@ -885,46 +891,56 @@ int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, 
     return Z2_OK;
 }
 
-int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, double s, const void *ref,
-               void *stream, z2_results *out) {
-    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
-    if (int rc = check_params(ctx, p)) return rc;
-    if (int rc = check_state(ctx, state)) return rc;
-    if (ref)
-        if (int rc = check_state(ctx, ref)) return rc;
-    const Lattice &L = lat->lat;
-    const int n = L.n_links, np = L.n_plaq;
-    const bool c128 = p->precision == Z2_C128;
-    cudaStream_t st = (cudaStream_t)stream;
-    // sigma^z-type: norm, plaquettes, 2x2 loop, contours, W_mu, sigma^z_l
-    std::vector<uint64_t> zm;
+// Observable masks of a lattice: sigma^z-type (norm, plaquettes, 2x2 loop,
+// contours, W_mu, sigma^z_l) and sigma^x-type (sigma^x_l, stars, V_mu).
+static void observable_masks(const Lattice &L, std::vector<uint64_t> &zm, std::vector<uint64_t> &xm) {
+    const int n = L.n_links;
+    zm.clear();
+    xm.clear();
     zm.push_back(0);
     for (auto m : L.plaq) zm.push_back(m);
     zm.push_back(L.wilson2x2);
     for (int k = 0; k < 3; ++k) zm.push_back(L.contour[k]);
     for (auto m : L.wmu) zm.push_back(m);
     for (int l = 0; l < n; ++l) zm.push_back(uint64_t(1) << l);
-    // sigma^x-type after the Hadamard layer: sigma^x_l, stars, V_mu
-    std::vector<uint64_t> xm;
     for (int l = 0; l < n; ++l) xm.push_back(uint64_t(1) << l);
     for (auto m : L.star) xm.push_back(m);
     for (auto m : L.vmu) xm.push_back(m);
+}
+
+// Enqueue every reduction of z2_measure on `st` into sc.d_out and its copy
+// to sc.h_out (no synchronisation).  Returns the number of doubles copied.
+static int measure_enqueue(z2_ctx *ctx, const z2_lattice *lat, int precision, void *state, const void *ref,
+                           cudaStream_t st, const Scratch &sc, int *n_out) {
+    const Lattice &L = lat->lat;
+    const int n = L.n_links;
+    const bool c128 = precision == Z2_C128;
+    std::vector<uint64_t> zm, xm;
+    observable_masks(L, zm, xm);
     const int nz = (int)zm.size(), nx = (int)xm.size();
     const int off_fid = nz + nx;  // <ref|psi> (2 doubles), then <ref|ref> (2 doubles)
     if (off_fid + 4 > OUT_DOUBLES) return fail(ctx, Z2_ERR_LATTICE, "too many observables");
-    if (int rc = zsums_device(ctx, n, c128, state, zm.data(), nz, 0, st)) return rc;
+    if (int rc = zsums_device(ctx, sc, n, c128, state, zm.data(), nz, 0, st)) return rc;
     if (ref) {
-        Z2_CUDA(ctx, launch_overlap(c128, ref, state, n, ctx->d_partials, ctx->d_out + off_fid, st));
-        Z2_CUDA(ctx, launch_overlap(c128, ref, ref, n, ctx->d_partials, ctx->d_out + off_fid + 2, st));
+        Z2_CUDA(ctx, launch_overlap(c128, ref, state, n, sc.d_partials, sc.d_out + off_fid, st));
+        Z2_CUDA(ctx, launch_overlap(c128, ref, ref, n, sc.d_partials, sc.d_out + off_fid + 2, st));
         ctx->launches += 4;
     }
-    if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
-    if (int rc = zsums_device(ctx, n, c128, state, xm.data(), nx, nz, st)) return rc;
-    if (int rc = z2_apply_hadamard(ctx, lat, p->precision, state, stream)) return rc;
-    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, (off_fid + 4) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    Z2_CUDA(ctx, cudaStreamSynchronize(st));
-    if (int rc = check_device_error(ctx)) return rc;
-    const double *h = ctx->h_out;
+    if (int rc = z2_apply_hadamard(ctx, lat, precision, state, st)) return rc;
+    if (int rc = zsums_device(ctx, sc, n, c128, state, xm.data(), nx, nz, st)) return rc;
+    if (int rc = z2_apply_hadamard(ctx, lat, precision, state, st)) return rc;
+    Z2_CUDA(ctx, cudaMemcpyAsync(sc.h_out, sc.d_out, (off_fid + 4) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    *n_out = off_fid + 4;
+    return Z2_OK;
+}
+
+// Turn the raw sums of measure_enqueue into the results struct.
+static void measure_finish(const Lattice &L, double lambda, double s, const double *h, bool has_ref, z2_results *out) {
+    const int n = L.n_links, np = L.n_plaq;
+    std::vector<uint64_t> zm, xm;
+    observable_masks(L, zm, xm);
+    const int nz = (int)zm.size(), nx = (int)xm.size();
+    const int off_fid = nz + nx;
     std::memset(out, 0, sizeof(*out));
     const double nan = std::nan("");
     // expectation values <psi|O|psi> / <psi|psi>: the norm differs from 1 only
@@ -959,8 +975,8 @@ int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void 
     }
     out->mean_star = ss / L.n_sites;
     for (int mu = 0; mu < L.d; ++mu) out->vmu[mu] = h[nz + n + L.n_sites + mu] * inv;
-    out->energy = -sx - s * p->lambda * sp;
-    if (ref) {
+    out->energy = -sx - s * lambda * sp;
+    if (has_ref) {
         // |<ref|psi>|^2 / (<ref|ref> <psi|psi>)
         const double rn = h[off_fid + 2];
         out->fidelity = (h[off_fid] * h[off_fid] + h[off_fid + 1] * h[off_fid + 1]) / (rn * nrm);
@@ -969,6 +985,21 @@ int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void 
         out->flags |= Z2_FLAG_NO_FIDELITY;
     }
     out->status = Z2_OK;
+}
+
+int z2_measure(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *state, double s, const void *ref,
+               void *stream, z2_results *out) {
+    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_params(ctx, p)) return rc;
+    if (int rc = check_state(ctx, state)) return rc;
+    if (ref)
+        if (int rc = check_state(ctx, ref)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int n_out = 0;
+    if (int rc = measure_enqueue(ctx, lat, p->precision, state, ref, st, ctx_scratch(ctx), &n_out)) return rc;
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    if (int rc = check_device_error(ctx)) return rc;
+    measure_finish(lat->lat, p->lambda, s, ctx->h_out, ref != nullptr, out);
     return Z2_OK;
 }
 
@@ -978,6 +1009,152 @@ int z2_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *sta
     if (int rc = z2_init_plus(ctx, lat, p->precision, state, stream)) return rc;
     if (int rc = z2_evolve(ctx, lat, p, state, 0, p->M, stream)) return rc;
     return z2_measure(ctx, lat, p, state, 1.0, ref, stream, out);
+}
+
+// ---------------------------------------------------------------------------
+// Batched runs.  A slot is a stream with its own state buffer and reduction
+// scratch; runs on one slot execute in stream order, slots run concurrently.
+struct RunSlot {
+    cudaStream_t st = nullptr;
+    void *state = nullptr;
+    double *d_partials = nullptr, *d_out = nullptr;
+};
+
+static void free_slots(std::vector<RunSlot> &slots) {
+    for (auto &sl : slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.state) cudaFree(sl.state);
+        if (sl.d_partials) cudaFree(sl.d_partials);
+        if (sl.d_out) cudaFree(sl.d_out);
+        if (sl.st) cudaStreamDestroy(sl.st);
+    }
+    slots.clear();
+}
+
+// |+>, the M steps and the observable reductions of one run, enqueued on st
+static int enqueue_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params &p, void *state, cudaStream_t st,
+                       const Scratch &sc) {
+    if (int rc = z2_init_plus(ctx, lat, p.precision, state, st)) return rc;
+    if (int rc = z2_evolve(ctx, lat, &p, state, 0, p.M, st)) return rc;
+    int n_out = 0;
+    return measure_enqueue(ctx, lat, p.precision, state, nullptr, st, sc, &n_out);
+}
+
+int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int32_t n_streams, z2_results *out) {
+    if (!ctx || (!specs && n > 0) || (!out && n > 0)) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (n < 0) return fail(ctx, Z2_ERR_ARG, "negative run count");
+    if (mode < Z2_SWEEP_PLAIN || mode > Z2_SWEEP_GRAPHS) return fail(ctx, Z2_ERR_ARG, "unknown sweep mode");
+    if (n == 0) return Z2_OK;
+    // lattices (shared between runs of the same shape) and plans, all built
+    // before any launch so that nothing allocates while runs are in flight
+    std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;
+    std::vector<const z2_lattice *> lat_of(n);
+    size_t max_bytes = 0;
+    int max_n = 8;
+    for (int i = 0; i < n; ++i) {
+        const auto &sp = specs[i];
+        out[i] = z2_results{};
+        if (int rc = check_params(ctx, &sp.params)) return rc;
+        int32_t L[3] = {sp.L[0], sp.L[1], sp.d == 3 ? sp.L[2] : 1};
+        auto key = std::make_tuple(sp.d, L[0], L[1], L[2]);
+        auto it = lats.find(key);
+        if (it == lats.end()) {
+            auto lat = std::make_unique<z2_lattice>();
+            std::string err;
+            if (!build_lattice(sp.d, L, lat->lat, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+            it = lats.emplace(key, std::move(lat)).first;
+        }
+        lat_of[i] = it->second.get();
+        const int nl = lat_of[i]->lat.n_links;
+        max_n = std::max(max_n, nl);
+        max_bytes = std::max<size_t>(max_bytes, size_t(sp.params.precision == Z2_C128 ? 16 : 8) << nl);
+        Plan *P = nullptr;
+        const std::string k1 = plan_key("evolve", lat_of[i]->lat, &sp.params, 0, sp.params.M, 0);
+        if (int rc = ensure_plan(ctx, k1, P, [&](Plan &Q) {
+                return build_evolve_plan(ctx, lat_of[i]->lat, sp.params, 0, sp.params.M, Q);
+            }))
+            return rc;
+        z2_run_params pp{};
+        pp.precision = sp.params.precision;
+        const std::string k2 = plan_key("had", lat_of[i]->lat, &pp, 0, 0, 0);
+        if (int rc = ensure_plan(ctx, k2, P, [&](Plan &Q) {
+                return build_hadamard_plan(ctx, lat_of[i]->lat, sp.params.precision == Z2_C128, Q);
+            }))
+            return rc;
+    }
+    const int S = mode == Z2_SWEEP_PLAIN ? 1 : std::max(1, std::min<int>(n_streams, std::min(n, 64)));
+    std::vector<RunSlot> slots(S);
+    double *h_all = nullptr;
+    auto cleanup = [&]() {
+        free_slots(slots);
+        if (h_all) cudaFreeHost(h_all);
+    };
+    const size_t partial_doubles = (size_t)reduce_blocks(max_n) * 32;
+    for (auto &sl : slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&sl.state, max_bytes) != cudaSuccess ||
+            cudaMalloc(&sl.d_partials, partial_doubles * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&sl.d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
+            cleanup();
+            return fail(ctx, Z2_ERR_OOM, "sweep: device allocation of the run slots failed");
+        }
+    }
+    if (cudaMallocHost(&h_all, (size_t)n * OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, Z2_ERR_OOM, "sweep: pinned host allocation failed");
+    }
+    std::vector<cudaGraphExec_t> execs;
+    int rc_all = Z2_OK;
+    for (int i = 0; i < n && rc_all == Z2_OK; ++i) {
+        RunSlot &sl = slots[i % S];
+        const Scratch sc{sl.d_partials, sl.d_out, h_all + (size_t)i * OUT_DOUBLES};
+        int rc = Z2_OK;
+        if (mode == Z2_SWEEP_GRAPHS) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            if (cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                rc = fail(ctx, Z2_ERR_CUDA, "sweep: stream capture failed to start");
+            } else {
+                rc = enqueue_run(ctx, lat_of[i], specs[i].params, sl.state, sl.st, sc);
+                cudaError_t e = cudaStreamEndCapture(sl.st, &g);
+                if (rc == Z2_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamEndCapture");
+                if (rc == Z2_OK) {
+                    e = cudaGraphInstantiate(&ge, g, 0);
+                    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaGraphInstantiate");
+                }
+                if (rc == Z2_OK) {
+                    e = cudaGraphLaunch(ge, sl.st);
+                    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaGraphLaunch");
+                    execs.push_back(ge);
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+        } else {
+            rc = enqueue_run(ctx, lat_of[i], specs[i].params, sl.state, sl.st, sc);
+            if (rc == Z2_OK && mode == Z2_SWEEP_PLAIN) {
+                cudaError_t e = cudaStreamSynchronize(sl.st);
+                if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamSynchronize");
+            }
+        }
+        out[i].status = rc;
+        if (rc != Z2_OK) rc_all = rc;
+    }
+    for (auto &sl : slots) {
+        cudaError_t e = cudaStreamSynchronize(sl.st);
+        if (e != cudaSuccess && rc_all == Z2_OK) rc_all = cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    for (auto ge : execs) cudaGraphExecDestroy(ge);
+    if (rc_all == Z2_OK) rc_all = check_device_error(ctx);
+    for (int i = 0; i < n; ++i) {
+        if (out[i].status == Z2_OK && rc_all == Z2_OK) {
+            measure_finish(lat_of[i]->lat, specs[i].params.lambda, 1.0, h_all + (size_t)i * OUT_DOUBLES, false,
+                           &out[i]);
+        } else if (out[i].status == Z2_OK) {
+            out[i].status = rc_all;
+        }
+    }
+    cleanup();
+    return rc_all;
 }
 
 }  // extern "C"

@@ -1,0 +1,85 @@
+"""Batched lambda sweep (z2_sweep): every mode gives each run exactly the
+result it has alone (same kernels on the same data in the same order), and
+the results agree with the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_1910_08020_gb300 as z2
+from oracle.lattice import Lattice as OLattice
+from paper_1910_08020_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    z2.build()
+    c = z2.Context(0)
+    yield c.handle
+    c.close()
+
+
+def small_specs(count=12, seed=5):
+    # the sweep's recipe with short schedules (oracle-sized) and small lattices
+    specs = workloads.sweep_specs(count, seed=seed,
+                                  lattices=[(2, (3, 3)), (2, (3, 2)), (2, (2, 2)), (2, (4, 2))])
+    for sp in specs:
+        sp["M"] = 10 + sp["M"] % 17
+        sp["T"] = 0.1 * sp["M"]
+    return specs
+
+
+def fields(r):
+    return np.array([r.energy, r.norm, r.mean_plaq, r.mean_star] + list(r.plaq[:9]) + list(r.sigmax[:18]))
+
+
+@pytest.mark.parametrize("mode", [z2.Z2_SWEEP_PLAIN, z2.Z2_SWEEP_STREAMS, z2.Z2_SWEEP_GRAPHS])
+def test_sweep_equals_single_runs(ctx, mode):
+    specs = small_specs()
+    res = z2.z2_sweep(ctx, specs, mode=mode, n_streams=4)
+    for sp, r in zip(specs, res):
+        assert r.status == 0
+        lat = z2.Lattice(sp["d"], sp["L"])
+        g = torch.empty(1 << lat.n_links, dtype=torch.complex64, device="cuda")
+        alone = z2.z2_run(ctx, lat.handle, z2.params(sp["lam"], sp["T"], sp["M"]), g)
+        assert np.array_equal(fields(r), fields(alone))
+
+
+def test_sweep_against_oracle(ctx):
+    specs = small_specs(6, seed=9)
+    res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_GRAPHS, n_streams=3)
+    for sp, r in zip(specs, res):
+        ol = OLattice(sp["d"], sp["L"])
+        ref = oracle.observables(ol, oracle.run(ol, sp["lam"], sp["T"], sp["M"], 1), sp["lam"])
+        S = ol.n_links + sp["lam"] * ol.n_plaq
+        assert abs(r.energy - ref["energy"]) < 1e-5 * S
+        assert np.max(np.abs(np.array(r.plaq[:ol.n_plaq]) - ref["plaq"])) < 1e-5
+
+
+def test_sweep_paper_mix_invariants(ctx):
+    # the 18q / 24q mix of the benchmark sweep, shortened: gauge invariants hold
+    specs = workloads.sweep_specs(8)
+    for sp in specs:
+        sp["M"] = 20
+        sp["T"] = 1.0
+    res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_STREAMS, n_streams=4)
+    for sp, r in zip(specs, res):
+        n_sites = int(np.prod(sp["L"]))
+        assert r.status == 0
+        assert abs(r.norm - 1) < 1e-5
+        assert np.max(np.abs(np.array(r.star[:n_sites]) - 1)) < 1e-5
+
+
+def test_sweep_errors(ctx):
+    specs = small_specs(2)
+    specs[1]["M"] = 0
+    with pytest.raises(z2.Z2Error):
+        z2.z2_sweep(ctx, specs)
+    with pytest.raises(z2.Z2Error):
+        z2.z2_sweep(ctx, small_specs(2), mode=7)
