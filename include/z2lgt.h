@@ -245,6 +245,43 @@ typedef struct {
  * kernels run on the same data in the same order). */
 int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int32_t n_streams, z2_results *out);
 
+/* ---- serving: a request loop with continuous batching --------------------
+ * A server owns a worker thread that admits submitted runs in arrival order
+ * as soon as a run slot is free and the run's device memory (its state plus
+ * reduction scratch) fits the HBM budget, starts each on its own stream (so
+ * runs that arrive while others are on the GPU overlap with them), keeps its
+ * state resident until it finishes, then returns the memory.  A run's result
+ * does not depend on what else is running.  While a server exists its
+ * context must not be used by other calls; all server calls are thread-safe. */
+typedef struct {
+    uint64_t submitted, completed, rejected, cancelled;
+    int32_t active;           /* runs currently on the GPU            */
+    int32_t queued;           /* runs waiting for admission           */
+    size_t hbm_in_use;        /* bytes held by active runs            */
+    size_t hbm_peak;          /* largest hbm_in_use so far            */
+} z2_serve_stats;
+
+/* hbm_budget: device bytes the server may hold for run states (0 = 80% of
+ * the free memory); max_slots: most runs on the GPU at once (1..64). */
+int z2_server_create(z2_ctx *ctx, size_t hbm_budget, int32_t max_slots, z2_server **out);
+/* Queue a run; *ticket identifies it.  Z2_ERR_BUDGET if it can never fit. */
+int z2_server_submit(z2_server *srv, const z2_run_spec *spec, uint64_t *ticket);
+/* *done = 1 once the run has finished (then *out holds its results, with
+ * out->status its status) or was cancelled; 0 while queued or running. */
+int z2_server_poll(z2_server *srv, uint64_t ticket, int32_t *done, z2_results *out);
+/* Block until the run has finished (or timeout_s seconds, < 0 = forever);
+ * Z2_ERR_DEVICE_TIMEOUT if the wait ran out. */
+int z2_server_wait(z2_server *srv, uint64_t ticket, double timeout_s, z2_results *out);
+/* Cancel a queued run (a running one finishes normally). */
+int z2_server_cancel(z2_server *srv, uint64_t ticket);
+int z2_server_stats(z2_server *srv, z2_serve_stats *out);
+/* Seconds a finished run waited for admission and spent running (host
+ * monotonic clock, submit -> admission -> completion seen by the worker). */
+int z2_server_request_times(z2_server *srv, uint64_t ticket, double *queued_s, double *run_s);
+/* Stop the worker after the runs already admitted finish; queued runs are
+ * cancelled; frees everything. */
+int z2_server_destroy(z2_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,9 @@ __all__ = [
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
     "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap",
-    "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs",
+    "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs", "ServeStats",
+    "z2_server_create", "z2_server_submit", "z2_server_poll", "z2_server_wait", "z2_server_cancel",
+    "z2_server_stats", "z2_server_request_times", "z2_server_destroy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -79,6 +81,12 @@ class RunSpec(ctypes.Structure):
 
 Z2_SWEEP_PLAIN, Z2_SWEEP_STREAMS, Z2_SWEEP_GRAPHS = 0, 1, 2
 
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("active", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)]
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
@@ -108,6 +116,14 @@ _SIGS = {
     "z2_zsums": [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
     "z2_overlap": [_P, _I, _I, _P, _P, ctypes.POINTER(_D), _P],
     "z2_sweep": [_P, ctypes.POINTER(RunSpec), _I, _I, _I, ctypes.POINTER(Results)],
+    "z2_server_create": [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)],
+    "z2_server_submit": [_P, ctypes.POINTER(RunSpec), ctypes.POINTER(ctypes.c_uint64)],
+    "z2_server_poll": [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(Results)],
+    "z2_server_wait": [_P, ctypes.c_uint64, _D, ctypes.POINTER(Results)],
+    "z2_server_cancel": [_P, ctypes.c_uint64],
+    "z2_server_stats": [_P, ctypes.POINTER(ServeStats)],
+    "z2_server_request_times": [_P, ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "z2_server_destroy": [_P],
 }
 
 
@@ -296,6 +312,59 @@ def z2_sweep(ctx, specs, mode=Z2_SWEEP_GRAPHS, n_streams=8):
     out = (Results * len(arr))()
     _check(load().z2_sweep(ctx, arr, len(arr), int(mode), int(n_streams), out), ctx)
     return list(out)
+
+
+def _scheck(rc, what):
+    if rc != Z2_OK:
+        raise Z2Error(rc, what)
+
+
+def z2_server_create(ctx, hbm_budget=0, max_slots=8):
+    out = _P()
+    _check(load().z2_server_create(ctx, int(hbm_budget), int(max_slots), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def z2_server_submit(srv, spec):
+    arr = run_specs([spec]) if isinstance(spec, dict) else spec
+    t = ctypes.c_uint64()
+    _scheck(load().z2_server_submit(srv, arr, ctypes.byref(t)), "server submit")
+    return t.value
+
+
+def z2_server_poll(srv, ticket):
+    done = _I()
+    res = Results()
+    rc = load().z2_server_poll(srv, ticket, ctypes.byref(done), ctypes.byref(res))
+    if rc not in (Z2_OK, -7):
+        raise Z2Error(rc, "server poll")
+    return bool(done.value), res
+
+
+def z2_server_wait(srv, ticket, timeout_s=-1.0):
+    res = Results()
+    rc = load().z2_server_wait(srv, ticket, float(timeout_s), ctypes.byref(res))
+    return rc, res
+
+
+def z2_server_cancel(srv, ticket):
+    return load().z2_server_cancel(srv, ticket)
+
+
+def z2_server_stats(srv):
+    st = ServeStats()
+    _scheck(load().z2_server_stats(srv, ctypes.byref(st)), "server stats")
+    return st
+
+
+def z2_server_request_times(srv, ticket):
+    q, r = _D(), _D()
+    _scheck(load().z2_server_request_times(srv, ticket, ctypes.byref(q), ctypes.byref(r)), "request times")
+    return q.value, r.value
+
+
+def z2_server_destroy(srv):
+    _scheck(load().z2_server_destroy(srv), "server destroy")
 
 
 def results_dict(res, info):

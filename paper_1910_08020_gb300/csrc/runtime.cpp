@@ -30,6 +30,11 @@
 #include <mutex>
 #include <tuple>
 
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -1155,6 +1160,322 @@ int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int
     }
     cleanup();
     return rc_all;
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop (continuous batching).
+}  // extern "C"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct ServeReq {
+    uint64_t id = 0;
+    z2_run_spec spec{};
+    int phase = 0;  // 0 queued, 1 running, 2 finished, 3 cancelled
+    size_t bytes = 0;
+    z2_results res{};
+    Clock::time_point t_submit, t_start, t_end;
+};
+
+struct ServeSlot {
+    cudaStream_t st = nullptr;
+    double *d_partials = nullptr, *d_out = nullptr, *h_out = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    uint64_t id = 0;
+    void *state = nullptr;
+    const z2_lattice *lat = nullptr;
+};
+
+}  // namespace
+
+struct z2_server {
+    z2_ctx *ctx = nullptr;
+    size_t budget = 0;
+    int max_slots = 1;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stopping = false;
+    std::map<uint64_t, ServeReq> reqs;
+    std::deque<uint64_t> queue;
+    uint64_t next_id = 1;
+    z2_serve_stats stats{};
+    std::vector<ServeSlot> slots;
+    std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;  // worker-owned
+    std::string last_error;
+};
+
+namespace {
+
+const z2_lattice *serve_lattice(z2_server *srv, const z2_run_spec &sp, std::string &err) {
+    int32_t L[3] = {sp.L[0], sp.L[1], sp.d == 3 ? sp.L[2] : 1};
+    auto key = std::make_tuple(sp.d, L[0], L[1], L[2]);
+    auto it = srv->lats.find(key);
+    if (it != srv->lats.end()) return it->second.get();
+    auto lat = std::make_unique<z2_lattice>();
+    if (!build_lattice(sp.d, L, lat->lat, err)) return nullptr;
+    return srv->lats.emplace(key, std::move(lat)).first->second.get();
+}
+
+void serve_worker(z2_server *srv) {
+    z2_ctx *ctx = srv->ctx;
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        bool progressed = false;
+        // retire finished runs
+        for (auto &sl : srv->slots) {
+            if (!sl.busy || cudaEventQuery(sl.ev) == cudaErrorNotReady) continue;
+            ServeReq &rq = srv->reqs[sl.id];
+            const cudaError_t e = cudaEventQuery(sl.ev);
+            if (e == cudaSuccess) {
+                measure_finish(sl.lat->lat, rq.spec.params.lambda, 1.0, sl.h_out, false, &rq.res);
+            } else {
+                rq.res.status = Z2_ERR_CUDA;
+            }
+            cudaFreeAsync(sl.state, sl.st);
+            srv->stats.hbm_in_use -= rq.bytes;
+            srv->stats.completed++;
+            srv->stats.active--;
+            rq.phase = 2;
+            rq.t_end = Clock::now();
+            sl.busy = false;
+            sl.state = nullptr;
+            progressed = true;
+        }
+        if (progressed) srv->cv_done.notify_all();
+        // admit in arrival order while a slot and the memory are free
+        while (!srv->queue.empty()) {
+            ServeReq &rq = srv->reqs[srv->queue.front()];
+            if (rq.phase == 3) {  // cancelled while queued
+                srv->queue.pop_front();
+                srv->stats.queued--;
+                continue;
+            }
+            ServeSlot *free_slot = nullptr;
+            for (auto &sl : srv->slots)
+                if (!sl.busy) {
+                    free_slot = &sl;
+                    break;
+                }
+            if (!free_slot || srv->stats.hbm_in_use + rq.bytes > srv->budget) break;
+            srv->queue.pop_front();
+            srv->stats.queued--;
+            rq.phase = 1;
+            rq.t_start = Clock::now();
+            srv->stats.active++;
+            srv->stats.hbm_in_use += rq.bytes;
+            srv->stats.hbm_peak = std::max(srv->stats.hbm_peak, srv->stats.hbm_in_use);
+            ServeSlot &sl = *free_slot;
+            sl.busy = true;
+            sl.id = rq.id;
+            const z2_run_spec spec = rq.spec;
+            lk.unlock();  // host-side planning and launches without the lock
+            std::string err;
+            int rc = Z2_OK;
+            const z2_lattice *lat = serve_lattice(srv, spec, err);
+            void *state = nullptr;
+            if (!lat) {
+                rc = Z2_ERR_LATTICE;
+            } else if (cudaMallocAsync(&state, rq.bytes, sl.st) != cudaSuccess) {
+                rc = Z2_ERR_OOM;
+            } else {
+                const Scratch sc{sl.d_partials, sl.d_out, sl.h_out};
+                rc = enqueue_run(ctx, lat, spec.params, state, sl.st, sc);
+                if (rc == Z2_OK && cudaEventRecord(sl.ev, sl.st) != cudaSuccess) rc = Z2_ERR_CUDA;
+            }
+            lk.lock();
+            sl.state = state;
+            sl.lat = lat;
+            if (rc != Z2_OK) {  // report at once, give the memory back
+                if (state) cudaFreeAsync(state, sl.st);
+                ServeReq &r2 = srv->reqs[sl.id];
+                r2.res.status = rc;
+                r2.phase = 2;
+                r2.t_end = Clock::now();
+                srv->stats.hbm_in_use -= r2.bytes;
+                srv->stats.active--;
+                srv->stats.completed++;
+                sl.busy = false;
+                sl.state = nullptr;
+                srv->cv_done.notify_all();
+            }
+            progressed = true;
+        }
+        const bool any_busy = std::any_of(srv->slots.begin(), srv->slots.end(), [](const ServeSlot &x) { return x.busy; });
+        if (srv->stopping && !any_busy && srv->queue.empty()) break;
+        if (!progressed) {
+            if (any_busy)
+                srv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else
+                srv->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int z2_server_create(z2_ctx *ctx, size_t hbm_budget, int32_t max_slots, z2_server **out) {
+    if (!ctx || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (max_slots < 1 || max_slots > 64) return fail(ctx, Z2_ERR_ARG, "max_slots must be 1..64");
+    *out = nullptr;
+    if (hbm_budget == 0) {
+        size_t fr = 0, tot = 0;
+        Z2_CUDA(ctx, cudaMemGetInfo(&fr, &tot));
+        hbm_budget = (size_t)(0.8 * (double)fr);
+    }
+    // keep freed run memory in the stream-ordered pool instead of returning it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    auto srv = std::make_unique<z2_server>();
+    srv->ctx = ctx;
+    srv->budget = hbm_budget;
+    srv->max_slots = max_slots;
+    srv->slots.resize(max_slots);
+    const size_t partial_doubles = (size_t)reduce_blocks(Z2_MAX_LINKS) * 32;
+    for (auto &sl : srv->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&sl.d_partials, partial_doubles * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&sl.d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&sl.h_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
+            for (auto &x : srv->slots) {
+                if (x.st) cudaStreamDestroy(x.st);
+                if (x.ev) cudaEventDestroy(x.ev);
+                if (x.d_partials) cudaFree(x.d_partials);
+                if (x.d_out) cudaFree(x.d_out);
+                if (x.h_out) cudaFreeHost(x.h_out);
+            }
+            return fail(ctx, Z2_ERR_OOM, "server: slot allocation failed");
+        }
+    }
+    z2_server *p = srv.release();
+    p->worker = std::thread(serve_worker, p);
+    *out = p;
+    return Z2_OK;
+}
+
+int z2_server_submit(z2_server *srv, const z2_run_spec *spec, uint64_t *ticket) {
+    if (!srv || !spec || !ticket) return Z2_ERR_ARG;
+    if (check_params(nullptr, &spec->params) != Z2_OK) return Z2_ERR_ARG;
+    Lattice probe;
+    std::string err;
+    int32_t L[3] = {spec->L[0], spec->L[1], spec->d == 3 ? spec->L[2] : 1};
+    if (!build_lattice(spec->d, L, probe, err)) return Z2_ERR_LATTICE;
+    const size_t bytes = (size_t)(spec->params.precision == Z2_C128 ? 16 : 8) << probe.n_links;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stopping) return Z2_ERR_CANCELLED;
+    if (bytes > srv->budget) {
+        srv->stats.rejected++;
+        return Z2_ERR_BUDGET;
+    }
+    ServeReq rq;
+    rq.id = srv->next_id++;
+    rq.spec = *spec;
+    rq.bytes = bytes;
+    rq.t_submit = Clock::now();
+    srv->reqs[rq.id] = rq;
+    srv->queue.push_back(rq.id);
+    srv->stats.submitted++;
+    srv->stats.queued++;
+    *ticket = rq.id;
+    srv->cv_work.notify_one();
+    return Z2_OK;
+}
+
+int z2_server_poll(z2_server *srv, uint64_t ticket, int32_t *done, z2_results *out) {
+    if (!srv || !done) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return Z2_ERR_NOT_FOUND;
+    *done = it->second.phase >= 2;
+    if (*done && out) *out = it->second.res;
+    return it->second.phase == 3 ? Z2_ERR_CANCELLED : Z2_OK;
+}
+
+int z2_server_wait(z2_server *srv, uint64_t ticket, double timeout_s, z2_results *out) {
+    if (!srv) return Z2_ERR_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return Z2_ERR_NOT_FOUND;
+    auto ready = [&] { return srv->reqs[ticket].phase >= 2; };
+    if (timeout_s < 0)
+        srv->cv_done.wait(lk, ready);
+    else if (!srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready))
+        return Z2_ERR_DEVICE_TIMEOUT;
+    const ServeReq &rq = srv->reqs[ticket];
+    if (out) *out = rq.res;
+    return rq.phase == 3 ? Z2_ERR_CANCELLED : rq.res.status;
+}
+
+int z2_server_cancel(z2_server *srv, uint64_t ticket) {
+    if (!srv) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return Z2_ERR_NOT_FOUND;
+    if (it->second.phase != 0) return Z2_ERR_ARG;  // running or finished: not cancellable
+    it->second.phase = 3;
+    it->second.res.status = Z2_ERR_CANCELLED;
+    it->second.t_end = Clock::now();
+    srv->stats.cancelled++;
+    srv->cv_done.notify_all();
+    return Z2_OK;
+}
+
+int z2_server_request_times(z2_server *srv, uint64_t ticket, double *queued_s, double *run_s) {
+    if (!srv || !queued_s || !run_s) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return Z2_ERR_NOT_FOUND;
+    const ServeReq &rq = it->second;
+    if (rq.phase != 2) return Z2_ERR_ARG;
+    *queued_s = std::chrono::duration<double>(rq.t_start - rq.t_submit).count();
+    *run_s = std::chrono::duration<double>(rq.t_end - rq.t_start).count();
+    return Z2_OK;
+}
+
+int z2_server_stats(z2_server *srv, z2_serve_stats *out) {
+    if (!srv || !out) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->stats;
+    return Z2_OK;
+}
+
+int z2_server_destroy(z2_server *srv) {
+    if (!srv) return Z2_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stopping = true;
+        for (auto id : srv->queue) {
+            ServeReq &rq = srv->reqs[id];
+            if (rq.phase == 0) {
+                rq.phase = 3;
+                rq.res.status = Z2_ERR_CANCELLED;
+                srv->stats.cancelled++;
+            }
+        }
+        srv->cv_work.notify_all();
+        srv->cv_done.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    for (auto &x : srv->slots) {
+        if (x.st) cudaStreamSynchronize(x.st);
+        if (x.st) cudaStreamDestroy(x.st);
+        if (x.ev) cudaEventDestroy(x.ev);
+        if (x.d_partials) cudaFree(x.d_partials);
+        if (x.d_out) cudaFree(x.d_out);
+        if (x.h_out) cudaFreeHost(x.h_out);
+    }
+    delete srv;
+    return Z2_OK;
 }
 
 }  // extern "C"
