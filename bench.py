@@ -152,6 +152,122 @@ def run_reference(args, wl, decomp):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Batched lambda sweep: 256 seeded runs (3x3 / 4x3 / 2x2x2 lattices,
+    lambda ~ U[0,6), T ~ U[5,20], M ~ U{100..400}, symmetric, complex64) in
+    each sweep mode; runs/s per mode, plans rebuilt inside every timed call."""
+    import torch
+
+    import paper_1910_08020_gb300 as z2
+    from paper_1910_08020_gb300 import workloads
+
+    torch.cuda.set_device(0)
+    ctx = z2.Context(0)
+    if args.variant:
+        z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_PASS_VARIANT, args.variant)
+    specs = workloads.sweep_specs(args.sweep_runs)
+    arr = z2.run_specs(specs)
+    steps = sum(sp["M"] for sp in specs)
+    warm = z2.run_specs(workloads.sweep_specs(6, seed=1))
+    for mode in (0, 1, 2):
+        z2.z2_sweep(ctx.handle, warm, mode=mode, n_streams=args.streams)
+    out = {}
+    for name, mode in (("plain", 0), ("streams", 1), ("graphs", 2)):
+        z2.z2_ctx_flush_plans(ctx.handle)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = z2.z2_sweep(ctx.handle, arr, mode=mode, n_streams=args.streams)
+        el = time.perf_counter() - t0
+        assert all(r.status == 0 for r in res)
+        out[name] = {"runs_per_s": len(specs) / el, "seconds": el, "trotter_steps_per_s": steps / el}
+    line = {"metric": "lambda-sweep runs/s", "value": out["graphs"]["runs_per_s"], "unit": "runs/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{len(specs)} adiabatic runs, lattices 3x3 (18q) / 4x3 (24q) / 2x2x2 (24q), "
+                                   "lambda~U[0,6), T~U[5,20], M~U{100..400}, symmetric, complex64, seed 20191018",
+                       "streams": args.streams, "total_trotter_steps": steps},
+            "modes": out, "speedup_vs_plain": {k: out[k]["runs_per_s"] / out["plain"]["runs_per_s"] for k in out}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    """Serving: a seeded Poisson request stream (lattices 2x2 .. 5x3 and
+    2x2x2, lambda ~ U[0,6], M ~ U{50..500}, T = 0.04 M, symmetric) submitted
+    on its own clock to the continuous-batching server, then the same stream
+    through the plain FIFO path (one run at a time, in arrival order)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_08020_gb300 as z2
+    from paper_1910_08020_gb300 import workloads
+
+    torch.cuda.set_device(0)
+    ctx = z2.Context(0)
+    lats = [l for l in workloads.SERVE_LATTICES if l[0] * int(np.prod(l[1])) <= args.serve_max_qubits]
+    reqs = workloads.poisson_stream(args.serve_count, rate=args.serve_rate, lattices=lats)
+    gpu_s_offered = None
+
+    def pct(v, q):
+        return float(np.percentile(np.array(v), q))
+
+    # warm-up: one request per lattice through both paths
+    for d, L in lats:
+        lat = z2.Lattice(d, L)
+        g = torch.empty(1 << lat.n_links, dtype=torch.complex64, device="cuda")
+        z2.z2_run(ctx.handle, lat.handle, z2.params(1.0, 2.0, 50), g)
+        del g
+    torch.cuda.synchronize()
+
+    srv = z2.z2_server_create(ctx.handle, hbm_budget=0, max_slots=args.serve_slots)
+    t0 = time.monotonic()
+    tickets = []
+    for rq in reqs:
+        delay = rq["arrival"] - (time.monotonic() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(z2.z2_server_submit(srv, rq))
+    lat_s = []
+    for tk in tickets:
+        rc, res = z2.z2_server_wait(srv, tk, timeout_s=3600)
+        assert rc == 0
+        q, r = z2.z2_server_request_times(srv, tk)
+        lat_s.append(q + r)
+    t_end = time.monotonic() - t0
+    st = z2.z2_server_stats(srv)
+    z2.z2_server_destroy(srv)
+    served = {"p50_s": pct(lat_s, 50), "p99_s": pct(lat_s, 99), "runs_per_s": len(reqs) / t_end,
+              "hbm_peak_gb": st.hbm_peak / 1e9, "slots": args.serve_slots}
+
+    # the plain FIFO path: one run at a time in arrival order
+    t0 = time.monotonic()
+    fifo = []
+    run_time = 0.0
+    for rq in reqs:
+        delay = rq["arrival"] - (time.monotonic() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        lat = z2.Lattice(rq["d"], rq["L"])
+        g = torch.empty(1 << lat.n_links, dtype=torch.complex64, device="cuda")
+        ts = time.monotonic()
+        z2.z2_run(ctx.handle, lat.handle, z2.params(rq["lam"], rq["T"], rq["M"]), g)
+        run_time += time.monotonic() - ts
+        fifo.append(time.monotonic() - t0 - rq["arrival"])
+        del g
+    t_fifo = time.monotonic() - t0
+    plain = {"p50_s": pct(fifo, 50), "p99_s": pct(fifo, 99), "runs_per_s": len(reqs) / t_fifo}
+    offered = run_time / reqs[-1]["arrival"]
+    line = {"metric": "serving p50/p99 latency and runs/s", "value": served["runs_per_s"], "unit": "runs/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} Poisson requests at {args.serve_rate}/s, lattices "
+                                   + ", ".join("x".join(map(str, L)) for _, L in lats)
+                                   + ", lambda~U[0,6], M~U{50..500}, T=0.04M, symmetric, complex64",
+                       "offered_gpu_seconds_per_second": offered},
+            "served": served, "plain_fifo": plain,
+            "speedup_runs_per_s": served["runs_per_s"] / plain["runs_per_s"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,11 +279,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA")
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--mode", default="run", choices=["run", "sweep", "serve"],
+                    help="run: the headline workload; sweep: batched lambda sweep; serve: request stream")
+    ap.add_argument("--sweep-runs", type=int, default=256)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-max-qubits", type=int, default=30)
+    ap.add_argument("--serve-slots", type=int, default=16)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     decomp = 1 if args.decomp == "sym" else 0
     if args.impl == "reference":
         run_reference(args, wl, decomp)
+        return
+    if args.mode == "sweep":
+        run_sweep(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
 
     import numpy as np
