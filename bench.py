@@ -406,8 +406,9 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "fidelity_ref": "device-resident reference state (|+>^N)"},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": f"pass_kernel_packed<{info.tile_bits},4,RX>" if args.variant != 2
-                         else f"pass_kernel_tma<float2,{info.tile_bits},RX>",
+            "roofline": {"bound": "hbm", "kernel": {0: f"pass_kernel_ring<{info.tile_bits},4,RX>", 1: f"pass_kernel_packed<{info.tile_bits},4,RX>",
+                                    2: f"pass_kernel_tma<float2,{info.tile_bits},RX>",
+                                    3: f"pass_kernel_ring<{info.tile_bits},4,RX>"}[args.variant],
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": None,
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},

@@ -148,7 +148,8 @@ int z2_ctx_flush_plans(z2_ctx *ctx);
 /* Execution options of a context (they change how, not what, is computed).
  * Setting one drops the cached plans. */
 #define Z2_OPT_TILE_BITS 0    /* 0 = automatic, else amplitudes per tile = 2^value (8..14)   */
-#define Z2_OPT_PASS_VARIANT 1 /* 0 = automatic, 1 = direct global loads, 2 = TMA-pipelined   */
+#define Z2_OPT_PASS_VARIANT 1 /* 0 = automatic, 1 = direct global loads, 2 = TMA per CTA,
+                                 3 = TMA ring (two tiles per CTA, complex64, multi-tile)      */
 int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
 
 /* ---- lattice (Sec. 2.1) ---------------------------------------------------

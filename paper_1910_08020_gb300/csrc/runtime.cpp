@@ -100,7 +100,7 @@ struct z2_ctx {
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
-    int variant = 0;  // 0 = automatic, 1 = direct loads, 2 = TMA per CTA, 3 = TMA ring (complex64)
+    int variant = 0;  // 0 = automatic (ring where it applies, else direct), 1 = direct, 2 = TMA per CTA, 3 = ring
     uint64_t launches = 0;
     int *d_err = nullptr;  // device flag: a bounded wait gave up
 };
@@ -392,8 +392,9 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
     for (auto &a : P.args) a.p0 = P.gate;
     P.tma = tma_possible(c128, P.geo.tb, ctx->variant) && encode_fn() != nullptr;
-    P.ring = !c128 && ctx->variant == 3 && P.geo.groups.size() > 1 && P.geo.tb >= 10 && P.geo.tb <= 13 &&
-             encode_fn() != nullptr;
+    // the ring variant is the automatic choice for multi-tile complex64 passes
+    P.ring = !c128 && (ctx->variant == 3 || ctx->variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
+             P.geo.tb <= 13 && encode_fn() != nullptr;
     return Z2_OK;
 }
 
