@@ -61,7 +61,6 @@ struct PassArgs {
     double scale;          // MID_SCALE factor
     const void *table;     // device phase table (np1 complex of the state's type)
     int tma_lo_bits;       // tile-id bits below the strided part (b - c of the TMA view)
-    const uint32_t *ptab;  // 4 x 256 plaquette parities of the tile-id bytes (device)
     uint32_t tcol[16];     // per tile bit: plaquette-membership mask of its global bit
     uint32_t colmask[64];  // per global bit (for the tile-id part)
 };

@@ -55,13 +55,6 @@ struct PassStep {
     double scale;
 };
 
-// plaquette parity vector of the tile-id bits: XOR of four per-byte tables
-__device__ __forceinline__ uint32_t tile_parity(const PassArgs &a, uint64_t tile) {
-    const uint32_t t32 = (uint32_t)tile;
-    return __ldg(a.ptab + (t32 & 255u)) ^ __ldg(a.ptab + 256 + ((t32 >> 8) & 255u)) ^
-           __ldg(a.ptab + 512 + ((t32 >> 16) & 255u)) ^ __ldg(a.ptab + 768 + (t32 >> 24));
-}
-
 __host__ __device__ constexpr int ctz_c(int x) { return (x & 1) ? 0 : 1 + ctz_c(x >> 1); }
 
 template <typename C>
@@ -251,7 +244,8 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, Tile<C, TB>::MINB) pass_kerne
         const uint64_t thi = tile >> (b - c);
         const uint64_t g0 = (tlo << c) | (thi << hib);
         // plaquette parity of the tile-id bits
-        const uint32_t ptile = tile_parity(a, tile);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
 
         C v[T::NE];
         const uint64_t stride = 1ull << sj;
@@ -431,7 +425,8 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, 1)
         // plaquette parity of the tile-id bits
         const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
-        const uint32_t ptile = tile_parity(a, tile);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
 
         C *sm = buf(cur);
         C v[T::NE];

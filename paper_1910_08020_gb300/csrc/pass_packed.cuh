@@ -120,27 +120,12 @@ __device__ __forceinline__ void prot(u64 (&re)[1 << W], u64 (&im)[1 << W], uint3
         for (int j = 0; j < T::NP; ++j) bfly_in_pair<OP>(re[j], im[j], t);
     }
     const uint32_t m = ((mask >> 1) & T::ownY(Q)) >> T::w0(Q);
-    if (OP == OP_RX_TAN) {
-        // branch-free: a level that is not rotated gets t = 0, an exact
-        // identity butterfly (a + 0 * b = a), so the registers never cross a
-        // data-dependent control-flow join
-        if (m == 0) return;
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const bool on = (m >> q) & 1u;
-            const u64 tq = on ? tt : 0ull, mq = on ? mt : 0ull;
+    for (int q = 0; q < W; ++q) {
+        if (m & (1u << q)) {
 #pragma unroll
             for (int j = 0; j < T::NP; ++j)
-                if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tq, mq);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-            if (m & (1u << q)) {
-#pragma unroll
-                for (int j = 0; j < T::NP; ++j)
-                    if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tt, mt);
-            }
+                if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tt, mt);
         }
     }
 }
@@ -316,7 +301,8 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
-        const uint32_t ptile = tile_parity(a, tile);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
 
         u64 re[T::NP], im[T::NP];
         {
@@ -454,7 +440,8 @@ __global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
         const uint64_t tile = gtile(n);
         const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
-        const uint32_t ptile = tile_parity(a, tile);
+        uint32_t ptile = 0;
+        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
 
         ulonglong2 *sm = buf(bi);
         u64 re[T::NP], im[T::NP];

@@ -79,14 +79,12 @@ struct Plan {
     bool flip = false;
     void *d_steps = nullptr;
     void *d_tables = nullptr;
-    uint32_t *d_ptab = nullptr;  // per group: 4 x 256 tile-id parity tables
     std::vector<PassArgs> args;  // per group
     bool tma = false;                  // TMA-pipelined persistent kernel
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
         if (d_tables) cudaFree(d_tables);
-        if (d_ptab) cudaFree(d_ptab);
     }
 };
 
@@ -393,30 +391,6 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     }
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
     for (auto &a : P.args) a.p0 = P.gate;
-    // tile-id parity tables: tile-id bit i sits at global bit c + i below the
-    // strided part and at b + tb - c + (i - (b - c)) above it
-    {
-        const size_t G = P.geo.groups.size();
-        std::vector<uint32_t> pt(G * 1024, 0);
-        for (size_t gi = 0; gi < G; ++gi) {
-            const Group &gr = P.geo.groups[gi];
-            const int lo = gr.b - gr.c, hib = gr.b + P.geo.tb - gr.c;
-            for (int byte = 0; byte < 4; ++byte)
-                for (int v = 0; v < 256; ++v) {
-                    uint32_t acc = 0;
-                    for (int j = 0; j < 8; ++j) {
-                        if (!((v >> j) & 1)) continue;
-                        const int i = 8 * byte + j;
-                        const int gpos = i < lo ? gr.c + i : hib + (i - lo);
-                        if (gpos < P.geo.n) acc ^= lat.colmask[gpos];
-                    }
-                    pt[gi * 1024 + byte * 256 + v] = acc;
-                }
-        }
-        Z2_CUDA(ctx, cudaMalloc(&P.d_ptab, pt.size() * sizeof(uint32_t)));
-        Z2_CUDA(ctx, cudaMemcpy(P.d_ptab, pt.data(), pt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        for (size_t gi = 0; gi < G; ++gi) P.args[gi].ptab = P.d_ptab + gi * 1024;
-    }
     P.tma = tma_possible(c128, P.geo.tb, ctx->variant) && encode_fn() != nullptr;
     // the ring variant is the automatic choice for multi-tile complex64 passes
     P.ring = !c128 && (ctx->variant == 3 || ctx->variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
