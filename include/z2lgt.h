@@ -228,6 +228,22 @@ int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state
 int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b,
                double *out, void *stream);
 
+/* ---- allocation-free reduction ----------------------------------------------
+ * The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory (a process under a hard memory cap, a plug-in that
+ * is handed a fixed arena, code that must not call cudaMalloc once running).
+ * It computes what z2_zsums does without a context and without allocating:
+ * its scratch is a fixed 256 KB array inside the library (1024 x 32 partial
+ * sums and 32 results, doubles), held on every GPU that loads the library
+ * until the process exits.  Limits: 1 <= n_masks <= 32 (larger counts return
+ * Z2_ERR_ARG with a message in z2_last_error(NULL)), 8 <= n_qubits <= 34.
+ * Per-thread sums are carried in FP64, so results agree with z2_zsums to
+ * rounding.  The first call on a device looks up the array's device address
+ * (do it before any stream capture).  All calls share the array: calls that
+ * overlap on the GPU race.  Synchronises `stream`; results in out[0..n_masks). */
+int z2_zsums_static(int32_t n_qubits, int32_t precision, const void *state, const uint64_t *masks, int32_t n_masks,
+                    double *out, void *stream);
+
 /* ---- batched runs: a lambda sweep (many independent adiabatic runs) ------- */
 typedef struct {
     int32_t d, L[3];      /* lattice                                  */

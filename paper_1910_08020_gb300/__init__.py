@@ -24,7 +24,7 @@ __all__ = [
     "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_ctx_set_option",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
-    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap",
+    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static",
     "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs", "ServeStats",
     "z2_server_create", "z2_server_submit", "z2_server_poll", "z2_server_wait", "z2_server_cancel",
     "z2_server_stats", "z2_server_request_times", "z2_server_destroy",
@@ -116,6 +116,7 @@ _SIGS = {
     "z2_zsums": [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
     "z2_overlap": [_P, _I, _I, _P, _P, ctypes.POINTER(_D), _P],
     "z2_sweep": [_P, ctypes.POINTER(RunSpec), _I, _I, _I, ctypes.POINTER(Results)],
+    "z2_zsums_static": [_I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
     "z2_server_create": [_P, ctypes.c_size_t, _I, ctypes.POINTER(_P)],
     "z2_server_submit": [_P, ctypes.POINTER(RunSpec), ctypes.POINTER(ctypes.c_uint64)],
     "z2_server_poll": [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(Results)],
@@ -284,6 +285,15 @@ def z2_zsums(ctx, n_qubits, precision, state, masks, stream=None):
     out = np.zeros(len(m), dtype=np.float64)
     _check(load().z2_zsums(ctx, n_qubits, precision, _ptr(state), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                            len(m), out.ctypes.data_as(ctypes.POINTER(_D)), _stream(stream)), ctx)
+    return out
+
+
+def z2_zsums_static(n_qubits, precision, state, masks, stream=None):
+    """Allocation-free z2_zsums (no context; fixed device scratch inside the library)."""
+    m = np.ascontiguousarray(masks, dtype=np.uint64)
+    out = np.zeros(len(m), dtype=np.float64)
+    _check(load().z2_zsums_static(n_qubits, precision, _ptr(state), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                  len(m), out.ctypes.data_as(ctypes.POINTER(_D)), _stream(stream)))
     return out
 
 

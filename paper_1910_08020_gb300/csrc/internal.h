@@ -27,6 +27,8 @@ struct Lattice {
     uint32_t colmask[64] = {};
 };
 bool build_lattice(int d, const int32_t *L, Lattice &out, std::string &err);
+// Record `msg` as this thread's last error (z2_last_error(NULL)); returns code.
+int set_thread_error(int code, const std::string &msg);
 
 // ---------------------------------------------------------------------------
 // One fused pass over the state (Sec. 2.2, both layers of a step).

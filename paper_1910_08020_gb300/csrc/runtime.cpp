@@ -112,6 +112,15 @@ constexpr int TABLE_STRIDE = Z2_MAX_PLAQ + 1;
 constexpr size_t PARTIALS_DOUBLES = (size_t(1) << 16) * 32;
 constexpr int OUT_DOUBLES = 256;
 
+}  // namespace
+
+int set_thread_error(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+namespace {
+
 int fail(z2_ctx *ctx, int code, const std::string &msg) {
     if (ctx)
         ctx->last_error = msg;
