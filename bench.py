@@ -100,6 +100,24 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def recorded_traffic(n):
+    """DRAM bytes per pass launch from the committed ncu record, scaled to n
+    qubits; None if the record is missing or the kernel source changed since."""
+    import hashlib
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "pass_kernel_ring_traffic.txt")):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split(None, 1)
+                rec[k] = v.strip()
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return float(rec["dram_bytes_per_launch"]) * 2.0 ** (n - int(rec["qubits"]))
+    except Exception:
+        return None
+
+
 def cpu_baseline(wl, decomp, budget_s=12.0):
     """The FP64 oracle (plain C, OpenMP over all host cores) on a bounded
     sample: symmetric/first-order Trotter steps of the 4x3 lattice (24 qubits,
@@ -410,7 +428,8 @@ def main():
                                     2: f"pass_kernel_tma<float2,{info.tile_bits},RX>",
                                     3: f"pass_kernel_ring<{info.tile_bits},4,RX>"}[args.variant],
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "traffic": recorded_traffic(n) if args.variant in (0, 3) and info.tile_bits <= 13 else None,
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},
             "e2e": {"value": e2e_v, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": ck,
