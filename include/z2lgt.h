@@ -152,6 +152,22 @@ int z2_ctx_flush_plans(z2_ctx *ctx);
                                  3 = TMA ring (two tiles per CTA, complex64, multi-tile)      */
 int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
 
+/* Autotuner: times each candidate execution plan of `lat` at `precision`
+ * (tile sizes x kernel variants; the tile size fixes how many qubits one pass
+ * fuses) on a few Trotter steps of `state` (a device state of that lattice
+ * and precision; its contents are overwritten), keeps the fastest for that
+ * qubit count and precision in the context (used when no explicit option is
+ * set) and, if the environment variable Z2_TUNE_CACHE names a file, records
+ * it there for later contexts.  Synchronises `stream`. */
+typedef struct {
+    int32_t tile_bits;     /* chosen tile size (qubits per tile)              */
+    int32_t variant;       /* chosen Z2_OPT_PASS_VARIANT value                */
+    double us_per_step;    /* measured time of one Trotter step               */
+    int32_t n_candidates;  /* candidates timed                                */
+} z2_tune_result;
+int z2_autotune(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, void *stream,
+                z2_tune_result *out);
+
 /* ---- lattice (Sec. 2.1) ---------------------------------------------------
  * d in {2, 3}; each L_mu >= 2; N = d * prod(L) <= Z2_MAX_LINKS and fits the
  * device.  Periodic boundaries only.  Host-only objects. */

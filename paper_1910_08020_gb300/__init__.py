@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "Z2Error", "RunParams", "Results", "LatticeInfo", "load", "build",
     "z2_ctx_create", "z2_ctx_destroy", "z2_last_error", "z2_version", "z2_ctx_launch_count",
-    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_ctx_set_option",
+    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_ctx_set_option", "z2_autotune", "TuneResult",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
     "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static",
@@ -65,6 +65,11 @@ class PlanInfo(ctypes.Structure):
                 ("n_launches", ctypes.c_int32), ("n_tables", ctypes.c_int32), ("flip", ctypes.c_int32)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int32), ("variant", ctypes.c_int32), ("us_per_step", ctypes.c_double),
+                ("n_candidates", ctypes.c_int32)]
+
+
 class Results(ctypes.Structure):
     _fields_ = [("s", ctypes.c_double), ("energy", ctypes.c_double), ("norm", ctypes.c_double),
                 ("mean_plaq", ctypes.c_double), ("wilson_2x2", ctypes.c_double), ("mean_star", ctypes.c_double),
@@ -98,6 +103,7 @@ _SIGS = {
     "z2_ctx_launch_count": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "z2_ctx_flush_plans": [_P],
     "z2_ctx_set_option": [_P, _I, _I],
+    "z2_autotune": [_P, _P, _I, _P, _P, ctypes.POINTER(TuneResult)],
     "z2_evolve_plan_info": [_P, _P, ctypes.POINTER(RunParams), _I, _I, ctypes.POINTER(PlanInfo)],
     "z2_last_error": [_P],
     "z2_version": [],
@@ -204,6 +210,12 @@ Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT = 0, 1
 
 def z2_ctx_set_option(ctx, option, value):
     _check(load().z2_ctx_set_option(ctx, int(option), int(value)), ctx)
+
+
+def z2_autotune(ctx, lat, precision, state, stream=None):
+    res = TuneResult()
+    _check(load().z2_autotune(ctx, lat, int(precision), _ptr(state), _stream(stream), ctypes.byref(res)), ctx)
+    return res
 
 
 def z2_ctx_flush_plans(ctx):

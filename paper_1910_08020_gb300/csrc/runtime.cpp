@@ -82,6 +82,7 @@ struct Plan {
     std::vector<PassArgs> args;  // per group
     bool tma = false;                  // TMA-pipelined persistent kernel
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
+    int variant = 0;                   // the kernel variant the plan was built for
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
         if (d_tables) cudaFree(d_tables);
@@ -101,6 +102,7 @@ struct z2_ctx {
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
     int variant = 0;  // 0 = automatic (ring where it applies, else direct), 1 = direct, 2 = TMA per CTA, 3 = ring
+    std::map<std::pair<int, int>, std::pair<int, int>> tuned;  // (qubits, precision) -> (tile bits, variant)
     uint64_t launches = 0;
     int *d_err = nullptr;  // device flag: a bounded wait gave up
 };
@@ -400,11 +402,23 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     }
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
     for (auto &a : P.args) a.p0 = P.gate;
-    P.tma = tma_possible(c128, P.geo.tb, ctx->variant) && encode_fn() != nullptr;
+    P.tma = tma_possible(c128, P.geo.tb, P.variant) && encode_fn() != nullptr;
     // the ring variant is the automatic choice for multi-tile complex64 passes
-    P.ring = !c128 && (ctx->variant == 3 || ctx->variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
+    P.ring = !c128 && (P.variant == 3 || P.variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
              P.geo.tb <= 13 && encode_fn() != nullptr;
     return Z2_OK;
+}
+
+// effective tile size and kernel variant for a state of n qubits: explicit
+// options first, then the autotuner's choice, else automatic
+std::pair<int, int> exec_choice(const z2_ctx *ctx, int n, int precision) {
+    int tb = ctx->tb_override, var = ctx->variant;
+    auto it = ctx->tuned.find({n, precision});
+    if (it != ctx->tuned.end()) {
+        if (!tb) tb = it->second.first;
+        if (!var) var = it->second.second;
+    }
+    return {tb, var};
 }
 
 // theta_k of the merged sequence for steps j0+1 .. j1 (k = j0 .. j1)
@@ -425,7 +439,9 @@ double theta_at(const z2_run_params &p, int k, int j0, int j1) {
 // Build the plan of steps j0+1 .. j1 (an empty plan when j0 == j1).
 int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, int j0, int j1, Plan &P) {
     std::string err;
-    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ctx->tb_override, ctx->variant, P.geo, err))
+    const auto ch = exec_choice(ctx, lat.n_links, p.precision);
+    P.variant = ch.second;
+    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ch.first, ch.second, P.geo, err))
         return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_RX_TAN;
     if (j1 == j0) return upload_plan(ctx, lat, P);
@@ -544,11 +560,14 @@ int check_device_error(z2_ctx *ctx) {
     return Z2_OK;
 }
 
-std::string plan_key(const char *kind, const Lattice &lat, const z2_run_params *p, int a, int b, double x) {
-    char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s|%d|%d,%d,%d|%a|%a|%d|%d|%d|%d|%d|%d|%a|%d", kind, lat.d, lat.L[0], lat.L[1],
+std::string plan_key(const z2_ctx *ctx, const char *kind, const Lattice &lat, const z2_run_params *p, int a, int b,
+                     double x) {
+    // the effective tile size and kernel variant are part of the key
+    const auto ch = exec_choice(ctx, lat.n_links, p ? p->precision : 0);
+    char buf[320];
+    std::snprintf(buf, sizeof(buf), "%s|%d|%d,%d,%d|%a|%a|%d|%d|%d|%d|%d|%d|%a|tb%d|v%d", kind, lat.d, lat.L[0], lat.L[1],
                   lat.L[2], p ? p->lambda : 0.0, p ? p->T : 0.0, p ? p->M : 0, p ? p->decomp : 0,
-                  p ? p->precision : 0, p ? p->sampling : 0, a, b, x, 0);
+                  p ? p->precision : 0, p ? p->sampling : 0, a, b, x, ch.first, ch.second);
     return buf;
 }
 
@@ -576,7 +595,9 @@ Plan *get_plan(z2_ctx *ctx, const std::string &key) {
 // Hadamard layer plan: every group once, scale 2^{-k/2} per group pass.
 int build_hadamard_plan(z2_ctx *ctx, const Lattice &lat, bool c128, Plan &P) {
     std::string err;
-    if (!plan_geometry(lat.n_links, c128, ctx->tb_override, ctx->variant, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+    const auto ch = exec_choice(ctx, lat.n_links, c128 ? Z2_C128 : Z2_C64);
+    P.variant = ch.second;
+    if (!plan_geometry(lat.n_links, c128, ch.first, ch.second, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_HADAMARD;
     for (int gi = 0; gi < (int)P.geo.groups.size(); ++gi) {
         HostPass hp{};
@@ -606,6 +627,15 @@ int ensure_plan(z2_ctx *ctx, const std::string &key, Plan *&out, const std::func
 }  // namespace z2
 
 using namespace z2;
+
+static std::string gpu_name(int device) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+    std::string n(prop.name);
+    for (auto &ch : n)
+        if (ch == ' ') ch = '_';
+    return n;
+}
 
 extern "C" {
 
@@ -637,6 +667,18 @@ int z2_ctx_create(int device, z2_ctx **out) {
         cudaFree(ctx->d_out);
         cudaFreeHost(ctx->h_out);
         return fail(nullptr, Z2_ERR_OOM, "context scratch allocation failed");
+    }
+    if (const char *path = std::getenv("Z2_TUNE_CACHE")) {
+        // lines "<gpu> <qubits> <precision> <tile bits> <variant> <us per step>"; later lines win
+        if (FILE *f = std::fopen(path, "r")) {
+            const std::string me = gpu_name(device);
+            char name[256];
+            int n, prec, tb, var;
+            double us;
+            while (std::fscanf(f, "%255s %d %d %d %d %lf", name, &n, &prec, &tb, &var, &us) == 6)
+                if (me == name && tb >= 0 && tb <= 14 && var >= 0 && var <= 3) ctx->tuned[{n, prec}] = {tb, var};
+            std::fclose(f);
+        }
     }
     if (const char *s = std::getenv("Z2_TILE_BITS")) ctx->tb_override = std::atoi(s);
     if (const char *s = std::getenv("Z2_PASS_VARIANT")) ctx->variant = std::string(s) == "direct" ? 1 : (std::string(s) == "tma" ? 2 : 0);
@@ -685,13 +727,87 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
     return Z2_OK;
 }
 
+int z2_autotune(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, void *stream,
+                z2_tune_result *out) {
+    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, state)) return rc;
+    const int n = lat->lat.n_links;
+    const bool c128 = precision == Z2_C128;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::pair<int, int>> cands;
+    if (n <= tile_limit(c128)) {
+        cands.push_back({0, 1});  // the whole state is one tile: nothing to choose
+    } else {
+        for (int tb = tile_limit(c128) - 2; tb <= tile_limit(c128); ++tb) {
+            if (tb >= n) continue;
+            cands.push_back({tb, 1});
+            if (!c128 && tb >= 10 && tb <= 13) cands.push_back({tb, 3});
+        }
+    }
+    const int saved_tb = ctx->tb_override, saved_var = ctx->variant;
+    z2_run_params p{};
+    const int S = 6;
+    p.lambda = 1.0;
+    p.T = 0.04 * S;
+    p.M = S;
+    p.decomp = Z2_SYMMETRIC;
+    p.precision = precision;
+    double best = 1e300;
+    std::pair<int, int> best_c = cands.front();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Z2_CUDA(ctx, cudaEventCreate(&e0));
+    Z2_CUDA(ctx, cudaEventCreate(&e1));
+    int rc = Z2_OK;
+    for (auto c : cands) {
+        ctx->tb_override = c.first;
+        ctx->variant = c.second;
+        if ((rc = z2_init_plus(ctx, lat, precision, state, st))) break;
+        if ((rc = z2_evolve(ctx, lat, &p, state, 0, S, st))) break;  // builds the plan, warms up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && rc == Z2_OK; ++r) rc = z2_evolve(ctx, lat, &p, state, 0, S, st);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(ctx, Z2_ERR_CUDA, "autotune: event synchronisation failed");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1000.0 * ms / (3 * S);
+        if (us < best) {
+            best = us;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tb_override = saved_tb;
+    ctx->variant = saved_var;
+    if (rc) return rc;
+    if (int e = check_device_error(ctx)) return e;
+    ctx->tuned[{n, precision}] = best_c;
+    out->tile_bits = best_c.first;
+    out->variant = best_c.second;
+    out->us_per_step = best;
+    out->n_candidates = (int)cands.size();
+    if (const char *path = std::getenv("Z2_TUNE_CACHE")) {
+        if (FILE *f = std::fopen(path, "a")) {
+            std::fprintf(f, "%s %d %d %d %d %.3f\n", gpu_name(ctx->device).c_str(), n, precision, best_c.first,
+                         best_c.second, best);
+            std::fclose(f);
+        }
+    }
+    return Z2_OK;
+}
+
 int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, int32_t j0, int32_t j1,
                         z2_plan_info *out) {
     if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
     if (int rc = check_params(ctx, p)) return rc;
     if (j0 < 0 || j1 > p->M || j0 > j1) return fail(ctx, Z2_ERR_ARG, "need 0 <= j0 <= j1 <= M");
     Plan *P = nullptr;
-    const std::string key = plan_key("evolve", lat->lat, p, j0, j1, 0);
+    const std::string key = plan_key(ctx, "evolve", lat->lat, p, j0, j1, 0);
     if (int rc = ensure_plan(ctx, key, P,
                              [&](Plan &Q) { return build_evolve_plan(ctx, lat->lat, *p, j0, j1, Q); }))
         return rc;
@@ -773,7 +889,7 @@ int z2_evolve(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *
     if (j0 < 0 || j1 > p->M || j0 > j1) return fail(ctx, Z2_ERR_ARG, "need 0 <= j0 <= j1 <= M");
     if (j0 == j1) return Z2_OK;
     Plan *P = nullptr;
-    const std::string key = plan_key("evolve", lat->lat, p, j0, j1, 0);
+    const std::string key = plan_key(ctx, "evolve", lat->lat, p, j0, j1, 0);
     if (int rc = ensure_plan(ctx, key, P,
                              [&](Plan &Q) { return build_evolve_plan(ctx, lat->lat, *p, j0, j1, Q); }))
         return rc;
@@ -788,10 +904,12 @@ int z2_apply_plaquettes(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, v
     Plan *P = nullptr;
     z2_run_params pp{};
     pp.precision = precision;
-    const std::string key = plan_key("plaq", lat->lat, &pp, 0, 0, theta);
+    const std::string key = plan_key(ctx, "plaq", lat->lat, &pp, 0, 0, theta);
     if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
             std::string err;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, ctx->variant, Q.geo, err))
+            const auto ch = exec_choice(ctx, lat->lat.n_links, precision);
+            Q.variant = ch.second;
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             push_table(Q, lat->lat, theta, {1, 0});
@@ -815,10 +933,12 @@ int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
     Plan *P = nullptr;
     z2_run_params pp{};
     pp.precision = precision;
-    const std::string key = plan_key("rx", lat->lat, &pp, 0, 0, dt);
+    const std::string key = plan_key(ctx, "rx", lat->lat, &pp, 0, 0, dt);
     if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
             std::string err;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ctx->tb_override, ctx->variant, Q.geo, err))
+            const auto ch = exec_choice(ctx, lat->lat.n_links, precision);
+            Q.variant = ch.second;
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             const GateSplit gs = split_gate(dt);
@@ -847,7 +967,7 @@ int z2_apply_hadamard(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
     Plan *P = nullptr;
     z2_run_params pp{};
     pp.precision = precision;
-    const std::string key = plan_key("had", lat->lat, &pp, 0, 0, 0);
+    const std::string key = plan_key(ctx, "had", lat->lat, &pp, 0, 0, 0);
     if (int rc = ensure_plan(ctx, key, P,
                              [&](Plan &Q) { return build_hadamard_plan(ctx, lat->lat, precision == Z2_C128, Q); }))
         return rc;
@@ -1084,14 +1204,14 @@ int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int
         max_n = std::max(max_n, nl);
         max_bytes = std::max<size_t>(max_bytes, size_t(sp.params.precision == Z2_C128 ? 16 : 8) << nl);
         Plan *P = nullptr;
-        const std::string k1 = plan_key("evolve", lat_of[i]->lat, &sp.params, 0, sp.params.M, 0);
+        const std::string k1 = plan_key(ctx, "evolve", lat_of[i]->lat, &sp.params, 0, sp.params.M, 0);
         if (int rc = ensure_plan(ctx, k1, P, [&](Plan &Q) {
                 return build_evolve_plan(ctx, lat_of[i]->lat, sp.params, 0, sp.params.M, Q);
             }))
             return rc;
         z2_run_params pp{};
         pp.precision = sp.params.precision;
-        const std::string k2 = plan_key("had", lat_of[i]->lat, &pp, 0, 0, 0);
+        const std::string k2 = plan_key(ctx, "had", lat_of[i]->lat, &pp, 0, 0, 0);
         if (int rc = ensure_plan(ctx, k2, P, [&](Plan &Q) {
                 return build_hadamard_plan(ctx, lat_of[i]->lat, sp.params.precision == Z2_C128, Q);
             }))

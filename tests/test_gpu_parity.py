@@ -283,3 +283,24 @@ def test_kernel_variants_and_tilings(ctx, variant, tile_bits, d, L):
     finally:
         z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 0)
         z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 0)
+
+
+@pytest.mark.parametrize("d,L", [(2, (3, 3)), (2, (4, 3)), (2, (2, 2))])
+def test_autotune_then_parity(ctx, d, L):
+    # the autotuner picks a tile size / kernel variant per qubit count; runs
+    # afterwards use it and still agree with the oracle
+    lat = z2.Lattice(d, L)
+    ol = OLattice(d, L)
+    g = torch.empty(1 << ol.n_links, dtype=torch.complex64, device="cuda")
+    tr = z2.z2_autotune(ctx, lat.handle, z2.Z2_C64, g)
+    assert tr.n_candidates >= 1 and tr.us_per_step > 0
+    if ol.n_links > 14:
+        assert tr.tile_bits in (12, 13, 14) and tr.variant in (1, 3)
+    lam, T, M = 2.0, 1.0, 12
+    psi = oracle.run(ol, lam, T, M, 1)
+    z2.z2_init_plus(ctx, lat.handle, z2.Z2_C64, g)
+    z2.z2_evolve(ctx, lat.handle, z2.params(lam, T, M), g, 0, M)
+    assert rel_err(host(g), psi) < 1e-5
+    if ol.n_links > 14:
+        info = z2.z2_evolve_plan_info(ctx, lat.handle, z2.params(lam, T, M), 0, M)
+        assert info.tile_bits == tr.tile_bits
