@@ -92,12 +92,35 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(elapsed_s, trotter_steps_per_rank, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank's Trotter
+    steps over the slowest rank's time (max over ranks, no data exchange)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    return elapsed_s, trotter_steps_per_rank * world / elapsed_s
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def kernel_name(variant, info):
+    """The pass kernel a plan runs (see z2_ctx_set_option / z2_autotune)."""
+    ring_ok = info.n_groups > 1 and 10 <= info.tile_bits <= 13
+    if variant in (0, 3) and ring_ok:
+        return f"pass_kernel_ring<{info.tile_bits},4,RX>"
+    if variant == 2:
+        return f"pass_kernel_tma<float2,{info.tile_bits},RX>"
+    return f"pass_kernel_packed<{info.tile_bits},4,RX>"
 
 
 def recorded_traffic(n):
@@ -297,6 +320,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA")
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner before the warm-up")
     ap.add_argument("--mode", default="run", choices=["run", "sweep", "serve"],
                     help="run: the headline workload; sweep: batched lambda sweep; serve: request stream")
     ap.add_argument("--sweep-runs", type=int, default=256)
@@ -343,6 +367,11 @@ def main():
     state = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
     ref = torch.empty_like(state)
     z2.z2_init_plus(ctx.handle, lat.handle, z2.Z2_C64, ref, stream)  # reference state for the fidelity
+    tune = None
+    if not args.no_autotune and not args.variant and not args.tile_bits:
+        tr = z2.z2_autotune(ctx.handle, lat.handle, z2.Z2_C64, state, stream)
+        tune = {"tile_bits": tr.tile_bits, "variant": tr.variant, "us_per_step": tr.us_per_step,
+                "candidates": tr.n_candidates}
     info = z2.z2_evolve_plan_info(ctx.handle, lat.handle, p, 0, wl["M"])
     state_bytes = lat.state_bytes(z2.Z2_C64)
 
@@ -381,12 +410,7 @@ def main():
     launches = z2.z2_ctx_launch_count(ctx.handle) - l0
     elapsed = t_start.elapsed_time(t_end) / 1000.0
     evolve_s = sum(a.elapsed_time(b) for a, b in ev_pass) / 1000.0
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    total_steps = wl["M"] * args.steps * world
-    value = total_steps / elapsed
+    elapsed, value = aggregate(elapsed, wl["M"] * args.steps, dist, device="cuda")
     pass_launches = info.n_passes * args.steps
     avg_pass = evolve_s / pass_launches
     alg_bytes = 2.0 * state_bytes  # read + write of the state per pass
@@ -422,14 +446,12 @@ def main():
                        "qubit_groups": info.n_groups, "passes_per_run": info.n_passes,
                        "l2": "state (%.1f GB) >> L2 (129 MB): no flush needed" % (state_bytes / 1e9),
                        "parallelism": f"replicas x{world}",
-                       "fidelity_ref": "device-resident reference state (|+>^N)"},
+                       "fidelity_ref": "device-resident reference state (|+>^N)", "autotune": tune},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": {0: f"pass_kernel_ring<{info.tile_bits},4,RX>", 1: f"pass_kernel_packed<{info.tile_bits},4,RX>",
-                                    2: f"pass_kernel_tma<float2,{info.tile_bits},RX>",
-                                    3: f"pass_kernel_ring<{info.tile_bits},4,RX>"}[args.variant],
+            "roofline": {"bound": "hbm", "kernel": kernel_name(args.variant or (tune or {}).get("variant", 0), info),
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind,
-                         "traffic": recorded_traffic(n) if args.variant in (0, 3) and info.tile_bits <= 13 else None,
+                         "traffic": recorded_traffic(n) if "ring<13" in kernel_name(args.variant or (tune or {}).get("variant", 0), info) else None,
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},
             "e2e": {"value": e2e_v, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": ck,
