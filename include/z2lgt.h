@@ -269,11 +269,15 @@ typedef struct {
 #define Z2_SWEEP_PLAIN 0   /* one run after another on one stream, each synchronised            */
 #define Z2_SWEEP_STREAMS 1 /* runs spread over n_streams streams, all enqueued before one wait  */
 #define Z2_SWEEP_GRAPHS 2  /* as STREAMS, each run (|+>, M steps, observables) one CUDA graph   */
+#define Z2_SWEEP_PERSISTENT 3 /* every complex64 run of >= 14 qubits evolved in one persistent
+                                 launch (gangs of co-resident CTAs take runs from a device queue);
+                                 observables and the other runs follow on n_streams streams    */
 
 /* Runs specs[0 .. n) (each: |+>^N, M steps, observables at s = 1, no
  * fidelity) and writes out[i]; out[i].status is that run's status.  The
  * library allocates and frees the device states (n_streams of the largest
- * size).  Returns Z2_OK if every run succeeded, else the first error.  The
+ * size; all states at once in PERSISTENT mode).  Returns Z2_OK if every run
+ * succeeded, else the first error.  The
  * result of a run does not depend on the mode or on the other runs (the same
  * kernels run on the same data in the same order). */
 int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int32_t n_streams, z2_results *out);

@@ -84,7 +84,7 @@ class RunSpec(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32 * 3), ("params", RunParams)]
 
 
-Z2_SWEEP_PLAIN, Z2_SWEEP_STREAMS, Z2_SWEEP_GRAPHS = 0, 1, 2
+Z2_SWEEP_PLAIN, Z2_SWEEP_STREAMS, Z2_SWEEP_GRAPHS, Z2_SWEEP_PERSISTENT = 0, 1, 2, 3
 
 
 class ServeStats(ctypes.Structure):

@@ -97,6 +97,26 @@ cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *ma
 cudaError_t launch_overlap(bool c128, const void *a, const void *b, int n, double *partials, double *d_out,
                            cudaStream_t st);
 int max_zsum_masks();
+// persistent multi-run evolution (persistent.cu): runs = device array of
+// PersistRun, ctl = zeroed control block, grid = a multiple of persist_gang()
+// no larger than persist_max_ctas(); runs need >= persist_tile_bits() qubits.
+cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st);
+int persist_tile_bits();
+int persist_gang();
+size_t persist_run_bytes();
+size_t persist_ctl_bytes();
+int persist_max_ctas(int sm_count);
+struct PersistRunHost {
+    void *state;
+    const void *steps;
+    const void *tables;
+    const void *args;
+    const int32_t *group;
+    int32_t n_passes;
+    int32_t n;
+    float init_amp;
+    int32_t pad;
+};
 int reduce_blocks(int n);
 
 struct PassStepHost {

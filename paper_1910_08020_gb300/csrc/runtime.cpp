@@ -1175,11 +1175,206 @@ static int enqueue_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params &
     return measure_enqueue(ctx, lat, p.precision, state, nullptr, st, sc, &n_out);
 }
 
+static int sweep_persistent(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t n_streams, z2_results *out) {
+    const int PT = persist_tile_bits();
+    // lattices and, for the runs the persistent kernel takes, plans with its tile size
+    std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;
+    std::vector<const z2_lattice *> lat_of(n);
+    std::vector<Plan *> plan_of(n, nullptr);
+    std::vector<char> persist(n, 0);
+    size_t total = 0;
+    int max_n = 8;
+    const int saved_tb = ctx->tb_override, saved_var = ctx->variant;
+    auto restore = [&]() {
+        ctx->tb_override = saved_tb;
+        ctx->variant = saved_var;
+    };
+    for (int i = 0; i < n; ++i) {
+        const auto &sp = specs[i];
+        out[i] = z2_results{};
+        if (int rc = check_params(ctx, &sp.params)) return rc;
+        int32_t L[3] = {sp.L[0], sp.L[1], sp.d == 3 ? sp.L[2] : 1};
+        auto key = std::make_tuple(sp.d, L[0], L[1], L[2]);
+        auto it = lats.find(key);
+        if (it == lats.end()) {
+            auto lat = std::make_unique<z2_lattice>();
+            std::string err;
+            if (!build_lattice(sp.d, L, lat->lat, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+            it = lats.emplace(key, std::move(lat)).first;
+        }
+        lat_of[i] = it->second.get();
+        const int nl = lat_of[i]->lat.n_links;
+        max_n = std::max(max_n, nl);
+        persist[i] = sp.params.precision == Z2_C64 && nl >= PT;
+        if (persist[i]) {
+            ctx->tb_override = PT;
+            ctx->variant = 1;
+            Plan *P = nullptr;
+            const std::string k1 = plan_key(ctx, "evolve", lat_of[i]->lat, &sp.params, 0, sp.params.M, 0);
+            int rc = ensure_plan(ctx, k1, P, [&](Plan &Q) {
+                return build_evolve_plan(ctx, lat_of[i]->lat, sp.params, 0, sp.params.M, Q);
+            });
+            restore();
+            if (rc) return rc;
+            if (P->geo.tb != PT) return fail(ctx, Z2_ERR_LATTICE, "persistent sweep: unexpected tile size");
+            plan_of[i] = P;
+            total += size_t(8) << nl;
+        }
+        // the observables use the context's normal plans
+        z2_run_params pp{};
+        pp.precision = sp.params.precision;
+        Plan *H = nullptr;
+        const std::string k2 = plan_key(ctx, "had", lat_of[i]->lat, &pp, 0, 0, 0);
+        if (int rc = ensure_plan(ctx, k2, H, [&](Plan &Q) {
+                return build_hadamard_plan(ctx, lat_of[i]->lat, sp.params.precision == Z2_C128, Q);
+            }))
+            return rc;
+    }
+    const int grid = (std::min(persist_max_ctas(ctx->sm_count), 64 * persist_gang()) / persist_gang()) * persist_gang();
+    if (grid <= 0) return fail(ctx, Z2_ERR_CUDA, "persistent sweep: kernel cannot be resident");
+    // device memory: every persistent run's state, the descriptors and the control block
+    std::vector<void *> states(n, nullptr);
+    void *d_runs = nullptr, *d_ctl = nullptr, *d_args = nullptr, *d_group = nullptr;
+    double *h_all = nullptr;
+    std::vector<RunSlot> slots(std::max(1, std::min<int>(n_streams, 64)));
+    auto cleanup = [&]() {
+        free_slots(slots);
+        for (void *p : states)
+            if (p) cudaFree(p);
+        if (d_runs) cudaFree(d_runs);
+        if (d_ctl) cudaFree(d_ctl);
+        if (d_args) cudaFree(d_args);
+        if (d_group) cudaFree(d_group);
+        if (h_all) cudaFreeHost(h_all);
+    };
+    std::vector<PersistRunHost> runs;
+    std::vector<int> run_index;
+    std::vector<PassArgs> all_args;
+    std::vector<int32_t> all_groups;
+    std::vector<size_t> args_off, group_off;
+    for (int i = 0; i < n; ++i) {
+        if (!persist[i]) continue;
+        args_off.push_back(all_args.size());
+        group_off.push_back(all_groups.size());
+        for (auto &a : plan_of[i]->args) all_args.push_back(a);
+        for (auto &hp : plan_of[i]->passes) all_groups.push_back(hp.group);
+    }
+    bool oom = false;
+    for (int i = 0; i < n && !oom; ++i) {
+        const size_t bytes = size_t(specs[i].params.precision == Z2_C128 ? 16 : 8) << lat_of[i]->lat.n_links;
+        if (persist[i] && cudaMalloc(&states[i], bytes) != cudaSuccess) oom = true;
+    }
+    if (oom || (!all_args.empty() && (cudaMalloc(&d_args, all_args.size() * sizeof(PassArgs)) != cudaSuccess ||
+                                      cudaMalloc(&d_group, all_groups.size() * sizeof(int32_t)) != cudaSuccess))) {
+        cleanup();
+        return fail(ctx, Z2_ERR_OOM, "persistent sweep: the run states do not fit the device");
+    }
+    {
+        int k = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!persist[i]) continue;
+            const Plan &P = *plan_of[i];
+            PersistRunHost r{};
+            r.state = states[i];
+            r.steps = P.d_steps;
+            r.tables = P.d_tables;
+            r.args = static_cast<PassArgs *>(d_args) + args_off[k];
+            r.group = static_cast<int32_t *>(d_group) + group_off[k];
+            r.n_passes = (int32_t)P.passes.size();
+            r.n = lat_of[i]->lat.n_links;
+            r.init_amp = (float)std::exp2(-0.5 * r.n);
+            runs.push_back(r);
+            run_index.push_back(i);
+            ++k;
+        }
+    }
+    const size_t partial_doubles = (size_t)reduce_blocks(max_n) * 32;
+    size_t max_bytes = 0;
+    for (int i = 0; i < n; ++i)
+        if (!persist[i])
+            max_bytes = std::max(max_bytes, size_t(specs[i].params.precision == Z2_C128 ? 16 : 8)
+                                                << lat_of[i]->lat.n_links);
+    for (auto &sl : slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            (max_bytes && cudaMalloc(&sl.state, max_bytes) != cudaSuccess) ||
+            cudaMalloc(&sl.d_partials, partial_doubles * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&sl.d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
+            cleanup();
+            return fail(ctx, Z2_ERR_OOM, "persistent sweep: slot allocation failed");
+        }
+    }
+    if (cudaMallocHost(&h_all, (size_t)n * OUT_DOUBLES * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d_ctl, persist_ctl_bytes()) != cudaSuccess ||
+        (!runs.empty() && cudaMalloc(&d_runs, runs.size() * sizeof(PersistRunHost)) != cudaSuccess)) {
+        cleanup();
+        return fail(ctx, Z2_ERR_OOM, "persistent sweep: allocation failed");
+    }
+    cudaStream_t st0 = slots[0].st;
+    int rc_all = Z2_OK;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && rc_all == Z2_OK) rc_all = cuda_fail(ctx, e, what);
+    };
+    if (!all_args.empty()) {
+        ck(cudaMemcpyAsync(d_args, all_args.data(), all_args.size() * sizeof(PassArgs), cudaMemcpyHostToDevice, st0),
+           "copy run arguments");
+        ck(cudaMemcpyAsync(d_group, all_groups.data(), all_groups.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           st0),
+           "copy pass groups");
+        ck(cudaMemcpyAsync(d_runs, runs.data(), runs.size() * sizeof(PersistRunHost), cudaMemcpyHostToDevice, st0),
+           "copy run descriptors");
+    }
+    ck(cudaMemsetAsync(d_ctl, 0, persist_ctl_bytes(), st0), "clear control block");
+    // 1) every persistent run evolved in one launch
+    if (!runs.empty() && rc_all == Z2_OK) {
+        ck(launch_persistent(d_runs, (int)runs.size(), d_ctl, ctx->d_err, grid, st0), "persistent launch");
+        ctx->launches += 1;
+        // odd numbers of quarter turns: the final all-qubit flip of those runs
+        for (size_t k = 0; k < runs.size() && rc_all == Z2_OK; ++k)
+            if (plan_of[run_index[k]]->flip) {
+                ck(launch_flip_all(false, runs[k].state, runs[k].n, ctx->sm_count * 8, st0), "flip");
+                ctx->launches += 1;
+            }
+    }
+    cudaEvent_t evolved = nullptr;
+    ck(cudaEventCreateWithFlags(&evolved, cudaEventDisableTiming), "event");
+    ck(cudaEventRecord(evolved, st0), "event record");
+    // 2) observables of those runs, then the remaining runs whole, on the slot streams
+    const int S = (int)slots.size();
+    for (auto &sl : slots) ck(cudaStreamWaitEvent(sl.st, evolved, 0), "stream wait");
+    int j = 0;
+    for (int i = 0; i < n && rc_all == Z2_OK; ++i) {
+        RunSlot &sl = slots[j++ % S];
+        const Scratch sc{sl.d_partials, sl.d_out, h_all + (size_t)i * OUT_DOUBLES};
+        int rc;
+        if (persist[i]) {
+            int n_out = 0;
+            rc = measure_enqueue(ctx, lat_of[i], Z2_C64, states[i], nullptr, sl.st, sc, &n_out);
+        } else {
+            rc = enqueue_run(ctx, lat_of[i], specs[i].params, sl.state, sl.st, sc);
+        }
+        out[i].status = rc;
+        if (rc) rc_all = rc;
+    }
+    for (auto &sl : slots) ck(cudaStreamSynchronize(sl.st), "cudaStreamSynchronize");
+    if (evolved) cudaEventDestroy(evolved);
+    if (rc_all == Z2_OK) rc_all = check_device_error(ctx);
+    for (int i = 0; i < n; ++i) {
+        if (out[i].status == Z2_OK && rc_all == Z2_OK)
+            measure_finish(lat_of[i]->lat, specs[i].params.lambda, 1.0, h_all + (size_t)i * OUT_DOUBLES, false,
+                           &out[i]);
+        else if (out[i].status == Z2_OK)
+            out[i].status = rc_all;
+    }
+    cleanup();
+    return rc_all;
+}
+
 int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int32_t n_streams, z2_results *out) {
     if (!ctx || (!specs && n > 0) || (!out && n > 0)) return fail(ctx, Z2_ERR_ARG, "NULL argument");
     if (n < 0) return fail(ctx, Z2_ERR_ARG, "negative run count");
-    if (mode < Z2_SWEEP_PLAIN || mode > Z2_SWEEP_GRAPHS) return fail(ctx, Z2_ERR_ARG, "unknown sweep mode");
+    if (mode < Z2_SWEEP_PLAIN || mode > Z2_SWEEP_PERSISTENT) return fail(ctx, Z2_ERR_ARG, "unknown sweep mode");
     if (n == 0) return Z2_OK;
+    if (mode == Z2_SWEEP_PERSISTENT) return sweep_persistent(ctx, specs, n, n_streams, out);
     // lattices (shared between runs of the same shape) and plans, all built
     // before any launch so that nothing allocates while runs are in flight
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;

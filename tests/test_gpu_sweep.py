@@ -83,3 +83,41 @@ def test_sweep_errors(ctx):
         z2.z2_sweep(ctx, specs)
     with pytest.raises(z2.Z2Error):
         z2.z2_sweep(ctx, small_specs(2), mode=7)
+
+
+def test_persistent_sweep(ctx):
+    # runs of >= 14 qubits go through the one persistent launch (2^14-amplitude
+    # tiles, direct kernel arithmetic), the others through the normal path
+    specs = small_specs(16, seed=11)
+    res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_PERSISTENT, n_streams=4)
+    for sp, r in zip(specs, res):
+        assert r.status == 0
+        lat = z2.Lattice(sp["d"], sp["L"])
+        g = torch.empty(1 << lat.n_links, dtype=torch.complex64, device="cuda")
+        default = z2.z2_run(ctx, lat.handle, z2.params(sp["lam"], sp["T"], sp["M"]), g)
+        # same kernel arithmetic as a single run planned with the same tiles
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 14 if lat.n_links >= 14 else 0)
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 1)
+        same = z2.z2_run(ctx, lat.handle, z2.params(sp["lam"], sp["T"], sp["M"]), g)
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 0)
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 0)
+        assert np.array_equal(fields(r), fields(same))
+        assert np.max(np.abs(fields(r) - fields(default))) < 1e-5 * (lat.n_links + sp["lam"] * lat.n_plaq)
+
+
+def test_persistent_sweep_paper_mix(ctx):
+    # the benchmark's lattices (18 and 24 qubits), shortened schedules, vs the oracle where small
+    specs = workloads.sweep_specs(10, seed=4)
+    for sp in specs:
+        sp["M"] = 8
+        sp["T"] = 0.4
+    res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_PERSISTENT, n_streams=3)
+    for sp, r in zip(specs, res):
+        assert r.status == 0
+        n_sites = int(np.prod(sp["L"]))
+        assert abs(r.norm - 1) < 1e-5
+        assert np.max(np.abs(np.array(r.star[:n_sites]) - 1)) < 1e-5
+        if sp["L"] == (3, 3):
+            ol = OLattice(sp["d"], sp["L"])
+            ref = oracle.observables(ol, oracle.run(ol, sp["lam"], sp["T"], sp["M"], 1), sp["lam"])
+            assert abs(r.energy - ref["energy"]) < 1e-5 * (ol.n_links + sp["lam"] * ol.n_plaq)
