@@ -95,12 +95,17 @@ def test_persistent_sweep(ctx):
         lat = z2.Lattice(sp["d"], sp["L"])
         g = torch.empty(1 << lat.n_links, dtype=torch.complex64, device="cuda")
         default = z2.z2_run(ctx, lat.handle, z2.params(sp["lam"], sp["T"], sp["M"]), g)
-        # same kernel arithmetic as a single run planned with the same tiles
-        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 14 if lat.n_links >= 14 else 0)
-        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 1)
-        same = z2.z2_run(ctx, lat.handle, z2.params(sp["lam"], sp["T"], sp["M"]), g)
+        # same kernel arithmetic as a single run evolved with the same tiles
+        # (observables with the context's default plans, as in the sweep)
+        p = z2.params(sp["lam"], sp["T"], sp["M"])
+        if lat.n_links >= 14:
+            z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 14)
+            z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 1)
+        z2.z2_init_plus(ctx, lat.handle, z2.Z2_C64, g)
+        z2.z2_evolve(ctx, lat.handle, p, g, 0, sp["M"])
         z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 0)
         z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 0)
+        same = z2.z2_measure(ctx, lat.handle, p, g)
         assert np.array_equal(fields(r), fields(same))
         assert np.max(np.abs(fields(r) - fields(default))) < 1e-5 * (lat.n_links + sp["lam"] * lat.n_plaq)
 
