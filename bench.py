@@ -116,6 +116,8 @@ def measured_peak():
 def kernel_name(variant, info):
     """The pass kernel a plan runs (see z2_ctx_set_option / z2_autotune)."""
     ring_ok = info.n_groups > 1 and 10 <= info.tile_bits <= 13
+    if variant == 4 and info.n_groups > 1 and 12 <= info.tile_bits <= 13:
+        return f"pass_kernel_ring<{info.tile_bits},5,RX>"
     if variant in (0, 3) and ring_ok:
         return f"pass_kernel_ring<{info.tile_bits},4,RX>"
     if variant == 2:
@@ -123,9 +125,10 @@ def kernel_name(variant, info):
     return f"pass_kernel_packed<{info.tile_bits},4,RX>"
 
 
-def recorded_traffic(n):
-    """DRAM bytes per pass launch from the committed ncu record, scaled to n
-    qubits; None if the record is missing or the kernel source changed since."""
+def recorded_traffic(n, kernel):
+    """DRAM bytes per pass launch of `kernel` from the committed ncu record,
+    scaled to n qubits; None if the record is missing, names another kernel,
+    or the kernel source changed since."""
     import hashlib
     try:
         rec = {}
@@ -133,6 +136,8 @@ def recorded_traffic(n):
             if line.strip() and not line.startswith("#"):
                 k, v = line.split(None, 1)
                 rec[k] = v.strip()
+        if rec["kernel"] != kernel:
+            return None
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
             return None
@@ -320,7 +325,7 @@ def main():
     ap.add_argument("--workload", default="4x4", choices=sorted(WORKLOADS))
     ap.add_argument("--decomp", default="sym", choices=["sym", "first"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA")
+    ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA, 3 ring, 4 ring with 32 pairs per thread")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner before the warm-up")
     ap.add_argument("--mode", default="run", choices=["run", "sweep", "serve"],
@@ -437,6 +442,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(wl, decomp)
     if rank == 0:
+        kname = kernel_name(args.variant or (tune or {}).get("variant", 0), info)
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True,
@@ -450,10 +456,10 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "fidelity_ref": "device-resident reference state (|+>^N)", "autotune": tune},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": kernel_name(args.variant or (tune or {}).get("variant", 0), info),
+            "roofline": {"bound": "hbm", "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind,
-                         "traffic": recorded_traffic(n) if "ring<13" in kernel_name(args.variant or (tune or {}).get("variant", 0), info) else None,
+                         "traffic": recorded_traffic(n, kname),
                          "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},
             "e2e": {"value": e2e_v, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": ck,

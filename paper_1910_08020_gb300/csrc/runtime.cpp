@@ -82,6 +82,7 @@ struct Plan {
     std::vector<PassArgs> args;  // per group
     bool tma = false;                  // TMA-pipelined persistent kernel
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
+    bool ring_wide = false;            // ... with 32 pairs per thread
     int variant = 0;                   // the kernel variant the plan was built for
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
@@ -101,7 +102,8 @@ struct z2_ctx {
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
-    int variant = 0;  // 0 = automatic (ring where it applies, else direct), 1 = direct, 2 = TMA per CTA, 3 = ring
+    int variant = 0;  // 0 = automatic (ring where it applies, else direct), 1 = direct, 2 = TMA per CTA, 3 = ring,
+                      // 4 = ring with 32 pairs per thread
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;  // (qubits, precision) -> (tile bits, variant)
     uint64_t launches = 0;
     int *d_err = nullptr;  // device flag: a bounded wait gave up
@@ -406,6 +408,9 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     // the ring variant is the automatic choice for multi-tile complex64 passes
     P.ring = !c128 && (P.variant == 3 || P.variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
              P.geo.tb <= 13 && encode_fn() != nullptr;
+    P.ring_wide = !c128 && P.variant == 4 && P.geo.groups.size() > 1 && P.geo.tb >= 12 && P.geo.tb <= 13 &&
+                  encode_fn() != nullptr;
+    if (P.ring_wide) P.ring = true;
     return Z2_OK;
 }
 
@@ -497,8 +502,12 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                 const int gi = P.passes[i].group;
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
-                Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
-                                                  ctx->d_err, grid, st));
+                if (P.ring_wide)
+                    Z2_CUDA(ctx, launch_pass_ring5_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
+                                                       ctx->d_err, grid, st));
+                else
+                    Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
+                                                      ctx->d_err, grid, st));
             }
             ctx->launches += P.passes.size();
             if (P.flip) {
@@ -676,7 +685,7 @@ int z2_ctx_create(int device, z2_ctx **out) {
             int n, prec, tb, var;
             double us;
             while (std::fscanf(f, "%255s %d %d %d %d %lf", name, &n, &prec, &tb, &var, &us) == 6)
-                if (me == name && tb >= 0 && tb <= 14 && var >= 0 && var <= 3) ctx->tuned[{n, prec}] = {tb, var};
+                if (me == name && tb >= 0 && tb <= 14 && var >= 0 && var <= 4) ctx->tuned[{n, prec}] = {tb, var};
             std::fclose(f);
         }
     }
@@ -717,7 +726,7 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
         if (value != 0 && (value < 8 || value > 14)) return fail(ctx, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
         ctx->tb_override = value;
     } else if (option == Z2_OPT_PASS_VARIANT) {
-        if (value < 0 || value > 3) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..3");
+        if (value < 0 || value > 4) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..4");
         ctx->variant = value;
     } else {
         return fail(ctx, Z2_ERR_ARG, "unknown option");
@@ -743,6 +752,7 @@ int z2_autotune(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *sta
             if (tb >= n) continue;
             cands.push_back({tb, 1});
             if (!c128 && tb >= 10 && tb <= 13) cands.push_back({tb, 3});
+            if (!c128 && tb >= 12 && tb <= 13) cands.push_back({tb, 4});
         }
     }
     const int saved_tb = ctx->tb_override, saved_var = ctx->variant;
