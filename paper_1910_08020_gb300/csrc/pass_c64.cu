@@ -62,7 +62,7 @@ static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    pass_kernel_ring<TB, PACK_W, OP><<<grid, 2 * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
+    pass_kernel_ring<TB, PACK_W, OP><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
     return cudaGetLastError();
 }
 

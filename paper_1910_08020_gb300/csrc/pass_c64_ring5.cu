@@ -24,7 +24,7 @@ cudaError_t launch_ring5_tb(const PassArgs &a, const CUtensorMap &m, const PassS
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    pass_kernel_ring<TB, RING5_W, OP><<<grid, 2 * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
+    pass_kernel_ring<TB, RING5_W, OP><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
     return cudaGetLastError();
 }
 

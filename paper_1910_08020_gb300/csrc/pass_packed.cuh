@@ -356,21 +356,30 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
 }
 
 // ---------------------------------------------------------------------------
-// Streaming variant: one CTA per SM made of two independent halves of NT
-// threads, each transforming its own tile with named barriers, fed by a ring
-// of three shared-memory tile buffers that the TMA unit fills ahead of use
-// (cp.async.bulk.tensor + mbarrier) and drains with TMA stores.  Local tile n
-// (global tile blockIdx.x + n * gridDim.x) lives in buffer n % 3 and is worked
-// on by half n % 2; when a half has stored tile n it refills that buffer with
-// tile n + 3, so two tiles are being transformed while the next one streams
-// in.  Multi-tile, single-step passes only (the host launches one per pass).
-// Requires pass_kernel.cuh (TMA and mbarrier helpers) to be included first.
+// Streaming variant: one CTA per SM made of NW independent workers of NT
+// threads, each transforming its own tile with its own named barrier, fed by a
+// ring of NB > NW shared-memory tile buffers that the TMA unit fills ahead of
+// use (cp.async.bulk.tensor + mbarrier) and drains with TMA stores.  Local
+// tile n (global tile blockIdx.x + n * gridDim.x) lives in buffer n % NB and
+// is worked on by worker n % NW; when a worker has stored tile n it refills
+// that buffer with tile n + NB, so NW tiles are being transformed while
+// NB - NW stream in.  Multi-tile, single-step passes only (the host launches
+// one per pass).  Requires pass_kernel.cuh (TMA and mbarrier helpers) to be
+// included first.
 template <int TB, int W>
 struct RingTile {
     using T = PTile<TB, W>;
     static constexpr uint32_t BUF = ((T::SLOTS * 16u + 1023u) / 1024u) * 1024u;
     static constexpr uint32_t TILE_BYTES = 8u << TB;
-    static constexpr uint32_t SMEM_BYTES = 3 * BUF + 1024;
+    // workers: up to 512 threads (256 with 32 pairs per thread, for the
+    // register file) and 8 named barriers; buffers: up to 2 per worker within
+    // 210 KB of shared memory
+    static constexpr int MAXT = W >= 5 ? 256 : 512;
+    static constexpr int NW = (MAXT / T::NT) < 8 ? (MAXT / T::NT) : 8;
+    static constexpr int NB_FIT = (int)((210u * 1024u) / BUF);
+    static constexpr int NB = NB_FIT < 2 * NW ? NB_FIT : 2 * NW;
+    static constexpr uint32_t SMEM_BYTES = NB * BUF + 1024;
+    static_assert(NW >= 1 && NB > NW, "ring needs more buffers than workers");
 };
 
 __device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
@@ -383,21 +392,25 @@ __device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
 }
 
 template <int TB, int W, int OP>
-__global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
+__global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     pass_kernel_ring(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
                      const PassStep *__restrict__ steps, const float2 *__restrict__ tables, int fmt, int *err) {
     using T = PTile<TB, W>;
     using RT = RingTile<TB, W>;
+    constexpr int NW = RT::NW, NB = RT::NB;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[3];
+    __shared__ __align__(8) uint64_t mbar[NB];
+    __shared__ uint32_t loads_issued[NB];  // TMA loads issued into each buffer
+    __shared__ uint32_t uses_seen[NB];     // loads of each buffer whose completion a worker has observed
+    __shared__ int abort_s;                // a worker gave up waiting
     __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
     // 1024-byte aligned start, as an offset into the shared array (keeps the
     // accesses in the shared address space)
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     auto buf = [&](int k) { return reinterpret_cast<ulonglong2 *>(base + k * RT::BUF); };
 
-    const uint32_t half = threadIdx.x / T::NT, t = threadIdx.x % T::NT;
-    const int bar = 1 + (int)half;
+    const uint32_t worker = threadIdx.x / T::NT, t = threadIdx.x % T::NT;
+    const int bar = 1 + (int)worker;
     const float gate = (float)a.p0;
     const int c = a.c, b = a.b, hib = b + TB - c, lo_bits = a.tma_lo_bits;
     const bool in_split = fmt & 1, out_split = fmt & 2;
@@ -407,36 +420,55 @@ __global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
     auto gtile = [&](uint64_t n) { return (uint64_t)blockIdx.x + n * gridDim.x; };
 
     if (st.mid == MID_TABLE)
-        for (uint32_t q = threadIdx.x; q < (uint32_t)a.np1; q += 2 * T::NT) {
+        for (uint32_t q = threadIdx.x; q < (uint32_t)a.np1; q += NW * T::NT) {
             const float2 e = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
             tabr[q] = e.x;
             tabi[q] = e.y;
         }
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 3; ++k) mbar_init(&mbar[k], 1);
+        for (int k = 0; k < NB; ++k) {
+            mbar_init(&mbar[k], 1);
+            loads_issued[k] = 0;
+            uses_seen[k] = 0;
+        }
+        abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (uint64_t n = 0; n < 3 && n < nloc; ++n) {
+        for (uint64_t n = 0; n < (uint64_t)NB && n < nloc; ++n) {
             const uint64_t g = gtile(n);
+            atomicAdd(&loads_issued[n], 1u);
             mbar_expect_tx(&mbar[n], RT::TILE_BYTES);
             tma_load_5d(buf((int)n), &tmap, &mbar[n], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
         }
 
-    for (uint64_t n = half; n < nloc; n += 2) {
-        const int bi = (int)(n % 3);
-        const uint32_t parity = (uint32_t)((n / 3) & 1);
+    for (uint64_t n = worker; n < nloc; n += NW) {
+        const int bi = (int)(n % NB);
+        const uint32_t use = (uint32_t)(n / NB);  // this tile is load number `use` of buffer bi
+        // Consecutive uses of a buffer belong to different workers, and this
+        // worker may arrive here while load `use - 1` is still in flight.  The
+        // barrier is then in phase use - 1, whose parity differs from ours, so
+        // the parity test would report the older phase use - 2 as done.  Wait
+        // first until the previous use has been observed: from then on the
+        // barrier's current phase is `use` and the test is exact.
         bool ok = false;
-        for (uint32_t k = 0; k < MBAR_POLL_LIMIT; ++k)
-            if ((ok = mbar_try_wait(&mbar[bi], parity))) break;
+        for (uint32_t k = 0; k < MBAR_POLL_LIMIT; ++k) {
+            if (*reinterpret_cast<volatile int *>(&abort_s)) break;
+            if (*reinterpret_cast<volatile uint32_t *>(&uses_seen[bi]) != use) continue;
+            if ((ok = mbar_try_wait(&mbar[bi], use & 1))) break;
+        }
         if (!bar_and(bar, T::NT, ok)) {
+            // this worker stops; the others stop at their next wait, and the
+            // CTA drains every copy still in flight before it exits
             if (t == 0) {
                 atomicExch(err, 1);
-                bulk_wait_all();
+                atomicExch(&abort_s, 1);
             }
-            return;
+            break;
         }
+        // every thread of this worker has seen the phase: publish it
+        if (t == 0) *reinterpret_cast<volatile uint32_t *>(&uses_seen[bi]) = use + 1;
         const uint64_t tile = gtile(n);
         const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
@@ -482,15 +514,28 @@ __global__ void __launch_bounds__(2 * PTile<TB, W>::NT, 1)
         tile_sync<T::NT>(bar);
         if (t == 0) {
             tma_store_5d(&tmap, sm, (int)(tile & ((1ull << lo_bits) - 1)), (int)(tile >> lo_bits));
-            if (n + 3 < nloc) {
+            if (n + NB < nloc) {
                 bulk_wait_read_all();  // the store has read the buffer
-                const uint64_t g = gtile(n + 3);
+                const uint64_t g = gtile(n + NB);
+                atomicAdd(&loads_issued[bi], 1u);
                 mbar_expect_tx(&mbar[bi], RT::TILE_BYTES);
                 tma_load_5d(sm, &tmap, &mbar[bi], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
             }
         }
     }
-    if (t == 0) bulk_wait_all();
+    if (t == 0) bulk_wait_all();  // this worker's stores
+    __syncthreads();
+    // Loads into a buffer are issued one at a time (a refill follows the use
+    // of the previous load), so waiting for the last one drains the buffer.
+    // After a normal run every load has been consumed and these return at once.
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t u = loads_issued[k];
+            if (!u) continue;
+            bool done = false;
+            for (uint32_t q = 0; q < MBAR_POLL_LIMIT && !done; ++q) done = mbar_try_wait(&mbar[k], (u - 1) & 1);
+            if (!done) atomicExch(err, 1);
+        }
 }
 
 }  // namespace z2
