@@ -451,6 +451,7 @@ def main():
             "config": {"workload": wl["name"], "decomp": "symmetric" if decomp else "first-order",
                        "step": "one whole adiabatic run (init, M Trotter steps, observables)",
                        "trotter_steps_per_bench_step": wl["M"], "tile_bits": info.tile_bits,
+                       "low_group_tile_bits": info.low_tile_bits,
                        "qubit_groups": info.n_groups, "passes_per_run": info.n_passes,
                        "l2": "state (%.1f GB) >> L2 (129 MB): no flush needed" % (state_bytes / 1e9),
                        "parallelism": f"replicas x{world}",

@@ -213,12 +213,15 @@ int z2_evolve(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *
  * so a step costs n_groups - 1 passes (1 when n_groups == 1, where the whole
  * state is one tile and the run is a single launch). */
 typedef struct {
-    int32_t tile_bits;   /* qubits held by one CTA tile                      */
-    int32_t n_groups;    /* qubit groups                                     */
-    int32_t n_passes;    /* streaming passes over the state                  */
-    int32_t n_launches;  /* kernel launches of the segment                   */
-    int32_t n_tables;    /* phase tables (one per plaquette layer)           */
-    int32_t flip;        /* 1 if a final all-qubit sigma^x flip is applied   */
+    int32_t tile_bits;      /* qubits held by one CTA tile                   */
+    int32_t n_groups;       /* qubit groups                                  */
+    int32_t n_passes;       /* streaming passes over the state               */
+    int32_t n_launches;     /* kernel launches of the segment                */
+    int32_t n_tables;       /* phase tables (one per plaquette layer)        */
+    int32_t flip;           /* 1 if a final all-qubit sigma^x flip is applied */
+    int32_t low_tile_bits;  /* tile of the low (contiguous) group's passes:
+                               tile_bits, or one less where the complex64
+                               ring runs that group on twice the workers    */
 } z2_plan_info;
 int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, int32_t j0, int32_t j1,
                         z2_plan_info *out);

@@ -62,7 +62,8 @@ class LatticeInfo(ctypes.Structure):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("n_passes", ctypes.c_int32),
-                ("n_launches", ctypes.c_int32), ("n_tables", ctypes.c_int32), ("flip", ctypes.c_int32)]
+                ("n_launches", ctypes.c_int32), ("n_tables", ctypes.c_int32), ("flip", ctypes.c_int32),
+                ("low_tile_bits", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):

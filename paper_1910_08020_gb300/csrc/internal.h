@@ -63,6 +63,8 @@ struct PassArgs {
     double scale;          // MID_SCALE factor
     const void *table;     // device phase table (np1 complex of the state's type)
     int tma_lo_bits;       // tile-id bits below the strided part (b - c of the TMA view)
+    int tma_hi_dim;        // TMA dimension of the upper tile-id bits: 4, or 3 for a split group
+    int hib;               // first global bit above the tile's lower range (ring kernel)
     uint32_t tcol[16];     // per tile bit: plaquette-membership mask of its global bit
     uint32_t colmask[64];  // per global bit (for the tile-id part)
 };

@@ -339,6 +339,22 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
         "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c4), "r"(smem_u32(bar))
         : "memory");
 }
+// the same with the tile coordinates in dimensions 1, 3 and 4 (the row and
+// strided coordinates, 0 and 2, are always 0 for a whole-tile box)
+__device__ __forceinline__ void tma_load_5c(void *dst, const CUtensorMap *map, uint64_t *bar, int c1, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %2, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_5c(const CUtensorMap *map, const void *src, int c1, int c3, int c4) {
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %1, %3, %4}], [%5];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(0), "r"(c1), "r"(c3), "r"(c4), "r"(smem_u32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
 __device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, const void *src, int c1, int c4) {
     asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %1, %1, %3}], [%4];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),

@@ -412,12 +412,20 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     const uint32_t worker = threadIdx.x / T::NT, t = threadIdx.x % T::NT;
     const int bar = 1 + (int)worker;
     const float gate = (float)a.p0;
-    const int c = a.c, b = a.b, hib = b + TB - c, lo_bits = a.tma_lo_bits;
+    // a group may be split in two bit ranges (see the host planner): the
+    // tile-id bits above the lower range start at a.hib, and the TMA view
+    // takes them in dimension 3 instead of 4
+    const int c = a.c, b = a.b, hib = a.hib, lo_bits = a.tma_lo_bits;
+    const bool hi3 = a.tma_hi_dim == 3;
     const bool in_split = fmt & 1, out_split = fmt & 2;
     const PassStep st = steps[0];
     const uint64_t ntiles = 1ull << (a.n - TB);
     const uint64_t nloc = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto gtile = [&](uint64_t n) { return (uint64_t)blockIdx.x + n * gridDim.x; };
+    auto load_tile = [&](void *dst, uint64_t *mb, uint64_t g) {
+        const int lo = (int)(g & ((1ull << lo_bits) - 1)), hi = (int)(g >> lo_bits);
+        tma_load_5c(dst, &tmap, mb, lo, hi3 ? hi : 0, hi3 ? 0 : hi);
+    };
 
     if (st.mid == MID_TABLE)
         for (uint32_t q = threadIdx.x; q < (uint32_t)a.np1; q += NW * T::NT) {
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
             const uint64_t g = gtile(n);
             atomicAdd(&loads_issued[n], 1u);
             mbar_expect_tx(&mbar[n], RT::TILE_BYTES);
-            tma_load_5d(buf((int)n), &tmap, &mbar[n], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
+            load_tile(buf((int)n), &mbar[n], g);
         }
 
     for (uint64_t n = worker; n < nloc; n += NW) {
@@ -513,13 +521,16 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
         fence_proxy_async();
         tile_sync<T::NT>(bar);
         if (t == 0) {
-            tma_store_5d(&tmap, sm, (int)(tile & ((1ull << lo_bits) - 1)), (int)(tile >> lo_bits));
+            {
+                const int lo = (int)(tile & ((1ull << lo_bits) - 1)), hi = (int)(tile >> lo_bits);
+                tma_store_5c(&tmap, sm, lo, hi3 ? hi : 0, hi3 ? 0 : hi);
+            }
             if (n + NB < nloc) {
                 bulk_wait_read_all();  // the store has read the buffer
                 const uint64_t g = gtile(n + NB);
                 atomicAdd(&loads_issued[bi], 1u);
                 mbar_expect_tx(&mbar[bi], RT::TILE_BYTES);
-                tma_load_5d(sm, &tmap, &mbar[bi], (int)(g & ((1ull << lo_bits) - 1)), (int)(g >> lo_bits));
+                load_tile(sm, &mbar[bi], g);
             }
         }
     }

@@ -51,9 +51,16 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// A group rotates k global bits: [b, b + k1) and, when k1 < k, also
+// [b2, b2 + k - k1) with b2 + k - k1 = n (a group split in two ranges, the
+// upper one ending at the top bit).  Its tiles hold the c lowest global bits
+// as passengers followed by the group's bits in increasing order.
 struct Group {
-    int lo = 0, hi = 0;  // global bits [lo, hi) rotated by this group
+    int lo = 0, hi = 0;  // for contiguous groups: global bits [lo, hi)
+    int tb = 0;          // tile bits of this group's passes
     int c = 0, b = 0;    // tile geometry
+    int k = 0, k1 = 0;   // rotated bits, and how many of them start at b
+    int b2 = 0;          // start of the upper range (split groups)
     uint32_t rot = 0;    // tile-bit mask of the group's bits
 };
 
@@ -154,6 +161,13 @@ bool tma_possible(bool c128, int tb, int variant) { return variant == 2 && tb <=
 // amplitudes, c = tb - k, with 3 <= c (>= 64-byte runs), c <= tb - R (the
 // register bits of the global layout lie in the strided part) and c <= 8 (7
 // for complex128; one TMA box row is at most 256 elements).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+
+// whether passes of this geometry run on the complex64 TMA ring kernel
+bool ring_plan(bool c128, int variant, int tb, int n_groups) {
+    return !c128 && (variant == 3 || variant == 0) && n_groups > 1 && tb >= 10 && tb <= 13 && encode_fn() != nullptr;
+}
+
 bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err) {
     g = Geometry{};
     g.n = n;
@@ -170,6 +184,8 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         Group gr;
         gr.lo = 0;
         gr.hi = n;
+        gr.tb = n;
+        gr.k = gr.k1 = n;
         gr.c = n;
         gr.b = n;
         gr.rot = (1u << n) - 1u;
@@ -208,12 +224,27 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         n_low = n - kmin(tb) * h;
         rem = kmin(tb) * h;
     }
+    // The complex64 ring kernel runs twice as many workers on tiles one bit
+    // smaller.  The low group (contiguous rows, no plaquette layer) gains from
+    // that more than it loses, so it takes the smaller tile whenever the
+    // strided groups can absorb the extra bit without an extra pass.
+    int tb_low = tb;
+    if (tb >= 11 && ring_plan(c128, variant, tb, h + 1) && n_low == tb) {
+        const int rem1 = n - (tb - 1);
+        if ((rem1 + kmax(tb) - 1) / kmax(tb) == h && rem1 >= kmin(tb) * h) {
+            tb_low = tb - 1;
+            n_low = tb_low;
+            rem = rem1;
+        }
+    }
     g.tb = tb;
     Group low;
     low.lo = 0;
     low.hi = n_low;
-    low.c = tb;
-    low.b = tb;
+    low.k = low.k1 = n_low;
+    low.tb = tb_low;
+    low.c = tb_low;
+    low.b = tb_low;
     low.rot = (n_low >= 32) ? 0xffffffffu : ((1u << n_low) - 1u);
     g.groups.push_back(low);
     int lo = n_low;
@@ -222,6 +253,8 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         Group gr;
         gr.lo = lo;
         gr.hi = lo + k;
+        gr.k = gr.k1 = k;
+        gr.tb = tb;
         gr.c = tb - k;
         gr.b = lo;
         gr.rot = ((1u << k) - 1u) << gr.c;
@@ -231,6 +264,53 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         }
         g.groups.push_back(gr);
         lo += k;
+    }
+    // Two strided groups on the ring: a tile's rows lie 2^b amplitudes apart,
+    // so each rotated bit at or above PAGE_BITS puts its rows on twice as many
+    // 2 MB pages, and address translation slows the copies down.  Split the
+    // pages' bits evenly: one group takes a few bits at the bottom of the
+    // strided range and the top ones, the other the middle ones.
+    if (h == 2 && ring_plan(c128, variant, tb, (int)g.groups.size())) {
+        constexpr int PAGE_BITS = 18;  // 2 MB / 8 bytes per complex64 amplitude
+        auto pages = [&](int lo_, int hi_) { return std::max(0, hi_ - std::max(lo_, PAGE_BITS)); };
+        const Group A = g.groups[1], B = g.groups[2];
+        const int base = A.lo;
+        int best = std::max(pages(A.lo, A.hi), pages(B.lo, B.hi)), best_a = -1, best_ks = 0;
+        for (int ks : {A.k, B.k}) {  // size of the split group
+            const int km = A.k + B.k - ks;
+            for (int a = 1; a < ks && a <= 8; ++a) {
+                if (ks - a > 8) continue;  // each range is one TMA box dimension (<= 256)
+                const int top_lo = n - (ks - a);
+                const int p = std::max(pages(base, base + a) + pages(top_lo, n), pages(base + a, base + a + km));
+                if (p < best) {
+                    best = p;
+                    best_a = a;
+                    best_ks = ks;
+                }
+            }
+        }
+        if (best_a > 0) {
+            const int ks = best_ks, km = A.k + B.k - ks, a = best_a;
+            Group S, Mi;
+            S.tb = Mi.tb = tb;
+            S.k = ks;
+            S.k1 = a;
+            S.b = base;
+            S.b2 = n - (ks - a);
+            S.c = tb - ks;
+            S.rot = ((1u << ks) - 1u) << S.c;
+            Mi.k = Mi.k1 = km;
+            Mi.lo = Mi.b = base + a;
+            Mi.hi = base + a + km;
+            Mi.c = tb - km;
+            Mi.rot = ((1u << km) - 1u) << Mi.c;
+            if (S.c < CMIN || Mi.c < CMIN || S.b < S.c || Mi.b < Mi.c || Mi.hi != S.b2) {
+                err = "internal tile planning error (split groups)";
+                return false;
+            }
+            g.groups[1] = S;
+            g.groups[2] = Mi;
+        }
     }
     // low group in the middle so that the merged boundary passes are the
     // cheaper strided ones
@@ -260,9 +340,28 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_tensor_map(CUtensorMap *m, void *state, int n, int tb, const Group &gr, bool c128, int &lo_bits) {
+bool make_tensor_map(CUtensorMap *m, void *state, int n, int tb, const Group &gr, bool c128, int &lo_bits,
+                     int &hi_dim) {
     auto enc = encode_fn();
     if (!enc) return false;
+    const uint64_t E = c128 ? 16 : 8;
+    if (gr.k1 < gr.k) {
+        // split group: (x_lo, tile_a, hi1, tile_b, hi2), box (2^c, 1, 2^k1, 1, 2^(k-k1))
+        const int c = gr.c, b = gr.b, k1 = gr.k1, k2 = gr.k - gr.k1, b2 = gr.b2;
+        if (c128 || b2 + k2 != n || b2 < b + k1) return false;
+        cuuint64_t dims[5] = {cuuint64_t(1) << c, cuuint64_t(1) << (b - c), cuuint64_t(1) << k1,
+                              cuuint64_t(1) << (b2 - b - k1), cuuint64_t(1) << k2};
+        cuuint64_t strides[4] = {(cuuint64_t(1) << c) * E, (cuuint64_t(1) << b) * E, (cuuint64_t(1) << (b + k1)) * E,
+                                 (cuuint64_t(1) << b2) * E};
+        cuuint32_t box[5] = {cuuint32_t(1) << c, 1, cuuint32_t(1) << k1, 1, cuuint32_t(1) << k2};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        lo_bits = b - c;
+        hi_dim = 3;
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, state, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    hi_dim = 4;
     int cp = gr.c, bp = gr.b;
     const int cmax = c128 ? 7 : 8;  // a box row holds at most 256 FLOAT64 elements
     if (cp > cmax) {                // contiguous tile: view it as 2^cmax x 2^(tb-cmax)
@@ -271,7 +370,6 @@ bool make_tensor_map(CUtensorMap *m, void *state, int n, int tb, const Group &gr
     }
     const int k = tb - cp, k1 = std::min(k, 8), k2 = k - k1;
     const int gap = bp - cp, top = n - bp - k;
-    const uint64_t E = c128 ? 16 : 8;
     const uint32_t inner = c128 ? 2u : 1u;  // FLOAT64 elements per amplitude
     cuuint64_t dims[5] = {(cuuint64_t(1) << cp) * inner, cuuint64_t(1) << gap, cuuint64_t(1) << k1,
                           cuuint64_t(1) << k2, cuuint64_t(1) << top};
@@ -292,9 +390,14 @@ PassArgs make_args(const Lattice &lat, const Geometry &g, const Group &gr) {
     a.n = g.n;
     a.c = gr.c;
     a.b = gr.b;
+    // first global bit above the tile's lower range: b + (tb - c) for a
+    // contiguous group (b itself for the low group, whose tile has no strided
+    // part), b + k1 for a split one
+    a.hib = gr.b + (gr.k1 < gr.k ? gr.k1 : gr.tb - gr.c);
+    a.tma_hi_dim = 4;
     a.np1 = lat.n_plaq + 1;
-    for (int i = 0; i < g.tb; ++i) {
-        const int gpos = i < gr.c ? i : gr.b + i - gr.c;
+    for (int i = 0; i < gr.tb; ++i) {
+        const int gpos = i < gr.c ? i : (i - gr.c < gr.k1 ? gr.b + i - gr.c : gr.b2 + i - gr.c - gr.k1);
         a.tcol[i] = gpos < 64 ? lat.colmask[gpos] : 0;
     }
     std::memcpy(a.colmask, lat.colmask, sizeof(a.colmask));
@@ -406,8 +509,7 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     for (auto &a : P.args) a.p0 = P.gate;
     P.tma = tma_possible(c128, P.geo.tb, P.variant) && encode_fn() != nullptr;
     // the ring variant is the automatic choice for multi-tile complex64 passes
-    P.ring = !c128 && (P.variant == 3 || P.variant == 0) && P.geo.groups.size() > 1 && P.geo.tb >= 10 &&
-             P.geo.tb <= 13 && encode_fn() != nullptr;
+    P.ring = ring_plan(c128, P.variant, P.geo.tb, (int)P.geo.groups.size());
     P.ring_wide = !c128 && P.variant == 4 && P.geo.groups.size() > 1 && P.geo.tb >= 12 && P.geo.tb <= 13 &&
                   encode_fn() != nullptr;
     if (P.ring_wide) P.ring = true;
@@ -467,7 +569,7 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
         for (int k = 0; k < G; ++k) {
             const int gi = g.order[fwd ? k : G - 1 - k];
             ev.push_back({0, gi, -1});
-            const int bits = g.groups[gi].hi - g.groups[gi].lo;
+            const int bits = g.groups[gi].k;
             pending *= std::pow(gs.c, bits) * ipow(gs.q * bits);
         }
         push_table(P, lat, theta_at(p, j, j0, j1), pending);
@@ -482,7 +584,7 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
 int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
     const auto &g = P.geo;
     const bool c128 = g.c128;
-    const uint64_t ntiles = 1ull << (g.n - g.tb);
+    const uint64_t ntiles = 1ull << (g.n - g.tb);  // of the main tile size
     const size_t step_bytes = sizeof(PassStepHost);
     const bool single = g.groups.size() == 1;
     if ((P.tma || P.ring) && !P.passes.empty()) {
@@ -490,23 +592,26 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
         // (a few microseconds) and passed by value to each launch
         std::vector<CUtensorMap> tmaps(g.groups.size());
         for (size_t i = 0; i < g.groups.size(); ++i) {
-            int lo_bits = 0;
-            if (!make_tensor_map(&tmaps[i], state, g.n, g.tb, g.groups[i], c128, lo_bits))
+            int lo_bits = 0, hi_dim = 4;
+            if (!make_tensor_map(&tmaps[i], state, g.n, g.groups[i].tb, g.groups[i], c128, lo_bits, hi_dim))
                 return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
             P.args[i].tma_lo_bits = lo_bits;
+            P.args[i].tma_hi_dim = hi_dim;
         }
         if (P.ring) {
-            const int grid = (int)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)ctx->sm_count);
             const size_t last = P.passes.size() - 1;
             for (size_t i = 0; i < P.passes.size(); ++i) {
                 const int gi = P.passes[i].group;
+                const int tb = g.groups[gi].tb;
+                const uint64_t nt = 1ull << (g.n - tb);
+                const int grid = (int)std::min<uint64_t>((nt + 1) / 2, (uint64_t)ctx->sm_count);
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
                 if (P.ring_wide)
-                    Z2_CUDA(ctx, launch_pass_ring5_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
+                    Z2_CUDA(ctx, launch_pass_ring5_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
                                                        ctx->d_err, grid, st));
                 else
-                    Z2_CUDA(ctx, launch_pass_ring_c64(g.tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
+                    Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
                                                       ctx->d_err, grid, st));
             }
             ctx->launches += P.passes.size();
@@ -546,8 +651,11 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
             for (size_t i = 0; i < P.passes.size(); ++i) {
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = c128 ? 0 : ((i > 0 ? 1 : 0) | (i < last ? 2 : 0));
-                Z2_CUDA(ctx, launch_pass_steps(c128, g.tb, P.op, state, P.args[P.passes[i].group], sp, 1,
-                                               P.d_tables, fmt, grid, st));
+                const int gi = P.passes[i].group;
+                const int tb = g.groups[gi].tb;
+                const int gr_grid = (int)std::min<uint64_t>(1ull << (g.n - tb), 1u << 20);
+                Z2_CUDA(ctx, launch_pass_steps(c128, tb, P.op, state, P.args[gi], sp, 1, P.d_tables, fmt, gr_grid,
+                                               st));
             }
             ctx->launches += P.passes.size();
         }
@@ -615,7 +723,7 @@ int build_hadamard_plan(z2_ctx *ctx, const Lattice &lat, bool c128, Plan &P) {
         hp.step.rot2 = 0;
         hp.step.mid = MID_SCALE;
         hp.step.table = -1;
-        hp.step.scale = std::pow(2.0, -0.5 * (P.geo.groups[gi].hi - P.geo.groups[gi].lo));
+        hp.step.scale = std::pow(2.0, -0.5 * P.geo.groups[gi].k);
         P.passes.push_back(hp);
     }
     return upload_plan(ctx, lat, P);
@@ -827,6 +935,7 @@ int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params 
     out->n_launches = (P->geo.groups.size() == 1 ? (P->passes.empty() ? 0 : 1) : (int)P->passes.size()) + (P->flip ? 1 : 0);
     out->n_tables = (int)(P->tables.size() / TABLE_STRIDE);
     out->flip = P->flip ? 1 : 0;
+    out->low_tile_bits = P->geo.groups.empty() ? 0 : P->geo.groups[0].tb;
     return Z2_OK;
 }
 
@@ -957,7 +1066,7 @@ int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
             std::complex<double> sc(1, 0);
             for (int gi : Q.geo.order) {
                 ev.push_back({0, gi, -1});
-                const int bits = Q.geo.groups[gi].hi - Q.geo.groups[gi].lo;
+                const int bits = Q.geo.groups[gi].k;
                 sc *= std::pow(gs.c, bits) * ipow(gs.q * bits);
             }
             push_table(Q, lat->lat, 0.0, sc);

@@ -304,3 +304,20 @@ def test_autotune_then_parity(ctx, d, L):
     if ol.n_links > 14:
         info = z2.z2_evolve_plan_info(ctx, lat.handle, z2.params(lam, T, M), 0, M)
         assert info.tile_bits == tr.tile_bits
+
+
+@pytest.mark.parametrize("variant,tile_bits,low,groups", [(3, 13, 12, 3), (3, 12, 11, 4), (1, 13, 13, 3), (4, 13, 13, 3)])
+def test_ring_low_group_tile(ctx, variant, tile_bits, low, groups):
+    # 32 qubits (4x4): the complex64 ring runs the low group on a tile one bit
+    # smaller (twice the workers) when the strided groups absorb the extra bit
+    # with no extra pass; the other kernels keep one tile size
+    lat = z2.Lattice(2, (4, 4))
+    z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, variant)
+    z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, tile_bits)
+    try:
+        info = z2.z2_evolve_plan_info(ctx, lat.handle, z2.params(3.0, 20.0, 500), 0, 500)
+        assert (info.tile_bits, info.low_tile_bits, info.n_groups) == (tile_bits, low, groups)
+        assert info.n_passes == 500 * (groups - 1) + 1
+    finally:
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_PASS_VARIANT, 0)
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_TILE_BITS, 0)
