@@ -119,6 +119,8 @@ def kernel_name(variant, info):
     if variant == 4 and info.n_groups > 1 and 12 <= info.tile_bits <= 13:
         return f"pass_kernel_ring<{info.tile_bits},5,RX>"
     if variant in (0, 3) and ring_ok:
+        if info.low_tile_bits != info.tile_bits:  # low group on the smaller tile
+            return f"pass_kernel_ring<{info.low_tile_bits},4,RX>+<{info.tile_bits},4,RX>"
         return f"pass_kernel_ring<{info.tile_bits},4,RX>"
     if variant == 2:
         return f"pass_kernel_tma<float2,{info.tile_bits},RX>"
