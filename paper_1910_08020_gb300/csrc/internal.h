@@ -85,8 +85,10 @@ cudaError_t launch_pass_tma(bool c128, int tb, int op, const PassArgs &a, const 
 int tma_tile_limit(bool c128);
 // complex64 streaming ring variant (pass_packed.cuh): multi-tile passes, one
 // step per launch, tile bits 10..13, grid = number of SMs
+// s8: relayouts through 8-byte (re | im) slot arrays instead of 16-byte pair
+// slots (used for strided passes, see pass_packed.cuh)
 cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st);
+                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8);
 // the same ring with 32 pairs per thread (pass_c64_ring5.cu), tile bits 12..13
 cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
                                   const void *tables, int fmt, int *err, int grid, cudaStream_t st);

@@ -50,19 +50,20 @@ cudaError_t launch_pass_c64(int tb, int op, void *psi, const PassArgs &a, const 
 
 int packed_threads(int tb) { return 1 << (tb - 1 - PACK_W); }
 
-template <int TB, int OP>
+template <int TB, int OP, bool S8 = false>
 static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps,
                                   const float2 *tables, int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, PACK_W>;
     using RT = RingTile<TB, PACK_W>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP>,
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP, S8>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    pass_kernel_ring<TB, PACK_W, OP><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
+    pass_kernel_ring<TB, PACK_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
+                                                                                      err);
     return cudaGetLastError();
 }
 
@@ -79,10 +80,16 @@ static cudaError_t launch_ring_op(int tb, const PassArgs &a, const CUtensorMap &
 }
 
 cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st) {
+                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8) {
     auto ps = static_cast<const PassStep *>(steps);
     auto tab = static_cast<const float2 *>(tables);
     const CUtensorMap &m = *static_cast<const CUtensorMap *>(tmap);
+    // 8-byte relayout scratch for the evolution's strided passes on 12- and
+    // 13-bit tiles (instruction-bound); the rest keep 16-byte pair slots
+    if (s8 && op == OP_RX_TAN && tb == 12)
+        return launch_ring_tb<12, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
+    if (s8 && op == OP_RX_TAN && tb == 13)
+        return launch_ring_tb<13, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
     return op == OP_HADAMARD ? launch_ring_op<OP_HADAMARD>(tb, a, m, ps, tab, fmt, err, grid, st)
                              : launch_ring_op<OP_RX_TAN>(tb, a, m, ps, tab, fmt, err, grid, st);
 }

@@ -11,8 +11,9 @@
 //     f32x2 FMA per amplitude;
 //   * a thread holds 2^W pairs; register layout q keeps the pair-index bits
 //     [w0(q), w0(q) + W) in registers, the remaining pair-index bits name the
-//     thread; changing layout moves 16-byte pairs through shared memory, one
-//     padding slot every 2^W pairs (conflict-free for every layout and size);
+//     thread; changing layout moves the pairs' 8-byte (re, re) and (im, im)
+//     halves through two shared-memory arrays, one padding slot every 2^W
+//     pairs (conflict-free for every layout and size);
 //   * between the passes of one evolution the state is stored "split": each
 //     16-byte pair as (re_x, re_x^1, im_x, im_x^1), so loads and stores need
 //     no register shuffles; the first and last pass convert from and to the
@@ -140,20 +141,48 @@ __device__ __forceinline__ void tile_sync(int bar) {
         asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
 }
 
-template <int TB, int W, int QA, int QB>
+// Relayout through shared memory.  S8 = false: one array of 16-byte
+// (re, re, im, im) pair slots.  S8 = true: the real and imaginary halves in
+// two arrays of T::SLOTS 8-byte slots (the same SLOTS * 16 bytes): 8-byte
+// accesses take each 64-bit register pair as it is, where a 16-byte access
+// needs re and im in four adjacent registers, which costs register moves
+// after the f32x2 butterflies; it also costs twice the load/store
+// instructions.  Both are conflict-free for every layout and tile size
+// (checked by enumeration; for S8 the 16 lanes of a half-warp always hit
+// distinct slots modulo 16).
+template <int TB, int W, int QA, int QB, bool S8>
 __device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm, uint32_t t,
                                           int bar = -1) {
     using T = PTile<TB, W>;
-    ulonglong2 *sa = sm + T::slot(T::base(QA, t));
+    if constexpr (S8) {
+        u64 *sr = reinterpret_cast<u64 *>(sm), *si = sr + T::SLOTS;
+        const uint32_t a = T::slot(T::base(QA, t));
 #pragma unroll
-    for (int j = 0; j < T::NP; ++j) sa[T::slot((uint32_t)j << T::w0(QA))] = make_ulonglong2(re[j], im[j]);
-    tile_sync<T::NT>(bar);
-    const ulonglong2 *sb = sm + T::slot(T::base(QB, t));
+        for (int j = 0; j < T::NP; ++j) {
+            const uint32_t o = a + T::slot((uint32_t)j << T::w0(QA));
+            sr[o] = re[j];
+            si[o] = im[j];
+        }
+        tile_sync<T::NT>(bar);
+        const uint32_t b = T::slot(T::base(QB, t));
 #pragma unroll
-    for (int j = 0; j < T::NP; ++j) {
-        const ulonglong2 v = sb[T::slot((uint32_t)j << T::w0(QB))];
-        re[j] = v.x;
-        im[j] = v.y;
+        for (int j = 0; j < T::NP; ++j) {
+            const uint32_t o = b + T::slot((uint32_t)j << T::w0(QB));
+            re[j] = sr[o];
+            im[j] = si[o];
+        }
+    } else {
+        ulonglong2 *sa = sm + T::slot(T::base(QA, t));
+#pragma unroll
+        for (int j = 0; j < T::NP; ++j) sa[T::slot((uint32_t)j << T::w0(QA))] = make_ulonglong2(re[j], im[j]);
+        tile_sync<T::NT>(bar);
+        const ulonglong2 *sb = sm + T::slot(T::base(QB, t));
+#pragma unroll
+        for (int j = 0; j < T::NP; ++j) {
+            const ulonglong2 v = sb[T::slot((uint32_t)j << T::w0(QB))];
+            re[j] = v.x;
+            im[j] = v.y;
+        }
     }
 }
 
@@ -218,32 +247,32 @@ __device__ __forceinline__ void pmid_in(int q, u64 (&re)[1 << W], u64 (&im)[1 <<
     }
 }
 
-template <int TB, int W, int QA>
+template <int TB, int W, int QA, bool S8>
 __device__ __forceinline__ void prelayout_from(int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
                                                uint32_t t, int bar) {
     constexpr int K = PTile<TB, W>::K;
     switch (qb) {
-        case 0: prelayout<TB, W, QA, 0>(re, im, sm, t, bar); break;
-        case 1: prelayout<TB, W, QA, (1 < K ? 1 : 0)>(re, im, sm, t, bar); break;
-        case 2: prelayout<TB, W, QA, (2 < K ? 2 : 0)>(re, im, sm, t, bar); break;
-        default: prelayout<TB, W, QA, (3 < K ? 3 : 0)>(re, im, sm, t, bar); break;
+        case 0: prelayout<TB, W, QA, 0, S8>(re, im, sm, t, bar); break;
+        case 1: prelayout<TB, W, QA, (1 < K ? 1 : 0), S8>(re, im, sm, t, bar); break;
+        case 2: prelayout<TB, W, QA, (2 < K ? 2 : 0), S8>(re, im, sm, t, bar); break;
+        default: prelayout<TB, W, QA, (3 < K ? 3 : 0), S8>(re, im, sm, t, bar); break;
     }
 }
 
-template <int TB, int W>
+template <int TB, int W, bool S8>
 __device__ __forceinline__ void prelayout_rt(int qa, int qb, u64 (&re)[1 << W], u64 (&im)[1 << W], ulonglong2 *sm,
                                              uint32_t t, int bar = -1) {
     constexpr int K = PTile<TB, W>::K;
     switch (qa) {
-        case 0: prelayout_from<TB, W, 0>(qb, re, im, sm, t, bar); break;
-        case 1: prelayout_from<TB, W, (1 < K ? 1 : 0)>(qb, re, im, sm, t, bar); break;
-        case 2: prelayout_from<TB, W, (2 < K ? 2 : 0)>(qb, re, im, sm, t, bar); break;
-        default: prelayout_from<TB, W, (3 < K ? 3 : 0)>(qb, re, im, sm, t, bar); break;
+        case 0: prelayout_from<TB, W, 0, S8>(qb, re, im, sm, t, bar); break;
+        case 1: prelayout_from<TB, W, (1 < K ? 1 : 0), S8>(qb, re, im, sm, t, bar); break;
+        case 2: prelayout_from<TB, W, (2 < K ? 2 : 0), S8>(qb, re, im, sm, t, bar); break;
+        default: prelayout_from<TB, W, (3 < K ? 3 : 0), S8>(qb, re, im, sm, t, bar); break;
     }
 }
 
 // one pass step on the registers of a tile (layout 0 in and out)
-template <int TB, int W, int OP>
+template <int TB, int W, int OP, bool S8 = false>
 __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, const PassArgs &a,
                                       float gate, uint32_t ptile, uint32_t t, ulonglong2 *sm, const float *tabr,
                                       const float *tabi, int bar) {
@@ -253,7 +282,7 @@ __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], cons
 #pragma unroll
     for (int q = 1; q < T::K; ++q) {
         if ((st.rot1 >> 1) & T::ownY(q)) {
-            prelayout_rt<TB, W>(cur, q, re, im, sm, t, bar);
+            prelayout_rt<TB, W, S8>(cur, q, re, im, sm, t, bar);
             cur = q;
             prot_in<TB, W, OP>(q, re, im, st.rot1, gate);
         }
@@ -264,13 +293,13 @@ __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], cons
 #pragma unroll
     for (int q = T::K - 1; q >= 1; --q) {
         if (q != first && ((st.rot2 >> 1) & T::ownY(q))) {
-            prelayout_rt<TB, W>(cur, q, re, im, sm, t, bar);
+            prelayout_rt<TB, W, S8>(cur, q, re, im, sm, t, bar);
             cur = q;
             prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, gate);
         }
     }
     if (cur != 0) {
-        prelayout_rt<TB, W>(cur, 0, re, im, sm, t, bar);
+        prelayout_rt<TB, W, S8>(cur, 0, re, im, sm, t, bar);
         if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, gate);
     }
 }
@@ -391,7 +420,7 @@ __device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
     return r != 0;
 }
 
-template <int TB, int W, int OP>
+template <int TB, int W, int OP, bool S8 = false>
 __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     pass_kernel_ring(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
                      const PassStep *__restrict__ steps, const float2 *__restrict__ tables, int fmt, int *err) {
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
             }
         }
         tile_sync<T::NT>(bar);  // dense reads done before the padded layouts reuse the buffer
-        pstep<TB, W, OP>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, bar);
+        pstep<TB, W, OP, S8>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, bar);
         tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
         if (out_split) {
 #pragma unroll

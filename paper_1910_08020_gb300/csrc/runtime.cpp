@@ -612,7 +612,7 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                                                        ctx->d_err, grid, st));
                 else
                     Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
-                                                      ctx->d_err, grid, st));
+                                                      ctx->d_err, grid, st, gi != 0));
             }
             ctx->launches += P.passes.size();
             if (P.flip) {
