@@ -118,6 +118,8 @@ def kernel_name(variant, info):
     ring_ok = info.n_groups > 1 and 10 <= info.tile_bits <= 13
     if variant == 4 and info.n_groups > 1 and 12 <= info.tile_bits <= 13:
         return f"pass_kernel_ring<{info.tile_bits},5,RX>"
+    if variant in (0, 5) and info.n_groups > 1 and 12 <= info.tile_bits <= 13:
+        return f"pass_kernel_ring<{info.low_tile_bits},4,RX>+<{info.tile_bits},5,RX>"
     if variant in (0, 3) and ring_ok:
         if info.low_tile_bits != info.tile_bits:  # low group on the smaller tile
             return f"pass_kernel_ring<{info.low_tile_bits},4,RX>+<{info.tile_bits},4,RX>"
@@ -327,9 +329,13 @@ def main():
     ap.add_argument("--workload", default="4x4", choices=sorted(WORKLOADS))
     ap.add_argument("--decomp", default="sym", choices=["sym", "first"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA, 3 ring, 4 ring with 32 pairs per thread")
+    ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA, 3 ring, 4 ring with 32 pairs per thread, "
+                    "5 ring with 32 pairs per thread on the strided groups")
     ap.add_argument("--tile-bits", type=int, default=0)
-    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner before the warm-up")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every tile size x kernel variant before the warm-up and run the fastest "
+                         "(default: the automatic plan)")
+    ap.add_argument("--no-autotune", action="store_true", help="(default) run the automatic plan")
     ap.add_argument("--mode", default="run", choices=["run", "sweep", "serve"],
                     help="run: the headline workload; sweep: batched lambda sweep; serve: request stream")
     ap.add_argument("--sweep-runs", type=int, default=256)
@@ -377,7 +383,7 @@ def main():
     ref = torch.empty_like(state)
     z2.z2_init_plus(ctx.handle, lat.handle, z2.Z2_C64, ref, stream)  # reference state for the fidelity
     tune = None
-    if not args.no_autotune and not args.variant and not args.tile_bits:
+    if args.autotune and not args.no_autotune and not args.variant and not args.tile_bits:
         tr = z2.z2_autotune(ctx.handle, lat.handle, z2.Z2_C64, state, stream)
         tune = {"tile_bits": tr.tile_bits, "variant": tr.variant, "us_per_step": tr.us_per_step,
                 "candidates": tr.n_candidates}

@@ -148,9 +148,12 @@ int z2_ctx_flush_plans(z2_ctx *ctx);
 /* Execution options of a context (they change how, not what, is computed).
  * Setting one drops the cached plans. */
 #define Z2_OPT_TILE_BITS 0    /* 0 = automatic, else amplitudes per tile = 2^value (8..14)   */
-#define Z2_OPT_PASS_VARIANT 1 /* 0 = automatic, 1 = direct global loads, 2 = TMA per CTA,
-                                 3 = TMA ring (two tiles per CTA, complex64, multi-tile),
-                                 4 = TMA ring with 32 pairs per thread (tile bits 12..13)    */
+#define Z2_OPT_PASS_VARIANT 1 /* 0 = automatic (as 5 where it applies, else 3, else 1),
+                                 1 = direct global loads, 2 = TMA per CTA,
+                                 3 = TMA ring (several tiles per CTA, complex64, multi-tile),
+                                 4 = TMA ring with 32 pairs per thread (tile bits 12..13),
+                                 5 = TMA ring, strided groups with 32 pairs per thread and
+                                     the low group with 16 (tile bits 12..13)               */
 int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
 
 /* Autotuner: times each candidate execution plan of `lat` at `precision`

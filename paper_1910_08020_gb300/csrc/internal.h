@@ -91,7 +91,7 @@ cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *
                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8);
 // the same ring with 32 pairs per thread (pass_c64_ring5.cu), tile bits 12..13
 cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st);
+                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8);
 int tma_smem_bytes(bool c128, int tb);
 size_t pass_smem(bool c128, int tb);
 cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream_t st);

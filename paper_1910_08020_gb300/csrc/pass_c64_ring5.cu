@@ -12,19 +12,20 @@ namespace z2 {
 namespace {
 constexpr int RING5_W = 5;
 
-template <int TB, int OP>
+template <int TB, int OP, bool S8 = false>
 cudaError_t launch_ring5_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps, const float2 *tables,
                             int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, RING5_W>;
     using RT = RingTile<TB, RING5_W>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, RING5_W, OP>,
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, RING5_W, OP, S8>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    pass_kernel_ring<TB, RING5_W, OP><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt, err);
+    pass_kernel_ring<TB, RING5_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
+                                                                                        err);
     return cudaGetLastError();
 }
 
@@ -40,10 +41,14 @@ cudaError_t launch_ring5_op(int tb, const PassArgs &a, const CUtensorMap &m, con
 }  // namespace
 
 cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st) {
+                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8) {
     auto ps = static_cast<const PassStep *>(steps);
     auto tab = static_cast<const float2 *>(tables);
     const CUtensorMap &m = *static_cast<const CUtensorMap *>(tmap);
+    if (s8 && op == OP_RX_TAN && tb == 12)
+        return launch_ring5_tb<12, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
+    if (s8 && op == OP_RX_TAN && tb == 13)
+        return launch_ring5_tb<13, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
     return op == OP_HADAMARD ? launch_ring5_op<OP_HADAMARD>(tb, a, m, ps, tab, fmt, err, grid, st)
                              : launch_ring5_op<OP_RX_TAN>(tb, a, m, ps, tab, fmt, err, grid, st);
 }

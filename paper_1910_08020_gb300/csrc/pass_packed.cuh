@@ -121,12 +121,30 @@ __device__ __forceinline__ void prot(u64 (&re)[1 << W], u64 (&im)[1 << W], uint3
         for (int j = 0; j < T::NP; ++j) bfly_in_pair<OP>(re[j], im[j], t);
     }
     const uint32_t m = ((mask >> 1) & T::ownY(Q)) >> T::w0(Q);
+    if constexpr (OP == OP_RX_TAN) {
+        // Every level of the layout runs, with gate 0 (an exact identity of
+        // the tan-form butterfly) where the bit is not rotated.  A branch per
+        // level would make the registers of the rotated and unrotated paths
+        // meet at its join, which costs a register move per amplitude and
+        // level; the spare FMAs are cheaper.
+        (void)tt;
+        (void)mt;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
-        if (m & (1u << q)) {
+        for (int q = 0; q < W; ++q) {
+            const float g = (m & (1u << q)) ? t : 0.0f;
+            const u64 tq = pk2(g, g), mq = pk2(-g, -g);
 #pragma unroll
             for (int j = 0; j < T::NP; ++j)
-                if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tt, mt);
+                if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tq, mq);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (m & (1u << q)) {
+#pragma unroll
+                for (int j = 0; j < T::NP; ++j)
+                    if (!(j & (1 << q))) bfly2<OP>(re[j], im[j], re[j | (1 << q)], im[j | (1 << q)], tt, mt);
+            }
         }
     }
 }

@@ -90,6 +90,7 @@ struct Plan {
     bool tma = false;                  // TMA-pipelined persistent kernel
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
     bool ring_wide = false;            // ... with 32 pairs per thread
+    bool strided_wide = false;         // ... for the strided groups only (variant 5)
     int variant = 0;                   // the kernel variant the plan was built for
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
@@ -165,7 +166,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 
 // whether passes of this geometry run on the complex64 TMA ring kernel
 bool ring_plan(bool c128, int variant, int tb, int n_groups) {
-    return !c128 && (variant == 3 || variant == 0) && n_groups > 1 && tb >= 10 && tb <= 13 && encode_fn() != nullptr;
+    return !c128 && (variant == 3 || variant == 0 || (variant == 5 && tb >= 12)) && n_groups > 1 && tb >= 10 &&
+           tb <= 13 && encode_fn() != nullptr;
 }
 
 bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err) {
@@ -513,6 +515,9 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     P.ring_wide = !c128 && P.variant == 4 && P.geo.groups.size() > 1 && P.geo.tb >= 12 && P.geo.tb <= 13 &&
                   encode_fn() != nullptr;
     if (P.ring_wide) P.ring = true;
+    // automatic: the strided groups on 32 pairs per thread where that kernel
+    // exists (measured fastest at 32 qubits: variant 5 over 3 and 4)
+    P.strided_wide = P.ring && (P.variant == 5 || (P.variant == 0 && P.geo.tb >= 12));
     return Z2_OK;
 }
 
@@ -607,9 +612,9 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                 const int grid = (int)std::min<uint64_t>((nt + 1) / 2, (uint64_t)ctx->sm_count);
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
-                if (P.ring_wide)
+                if (P.ring_wide || (P.strided_wide && gi != 0))
                     Z2_CUDA(ctx, launch_pass_ring5_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
-                                                       ctx->d_err, grid, st));
+                                                       ctx->d_err, grid, st, P.strided_wide));
                 else
                     Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
                                                       ctx->d_err, grid, st, gi != 0));
@@ -793,7 +798,7 @@ int z2_ctx_create(int device, z2_ctx **out) {
             int n, prec, tb, var;
             double us;
             while (std::fscanf(f, "%255s %d %d %d %d %lf", name, &n, &prec, &tb, &var, &us) == 6)
-                if (me == name && tb >= 0 && tb <= 14 && var >= 0 && var <= 4) ctx->tuned[{n, prec}] = {tb, var};
+                if (me == name && tb >= 0 && tb <= 14 && var >= 0 && var <= 5) ctx->tuned[{n, prec}] = {tb, var};
             std::fclose(f);
         }
     }
@@ -834,7 +839,7 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
         if (value != 0 && (value < 8 || value > 14)) return fail(ctx, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
         ctx->tb_override = value;
     } else if (option == Z2_OPT_PASS_VARIANT) {
-        if (value < 0 || value > 4) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..4");
+        if (value < 0 || value > 5) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..5");
         ctx->variant = value;
     } else {
         return fail(ctx, Z2_ERR_ARG, "unknown option");
@@ -861,11 +866,12 @@ int z2_autotune(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *sta
             cands.push_back({tb, 1});
             if (!c128 && tb >= 10 && tb <= 13) cands.push_back({tb, 3});
             if (!c128 && tb >= 12 && tb <= 13) cands.push_back({tb, 4});
+            if (!c128 && tb >= 12 && tb <= 13) cands.push_back({tb, 5});
         }
     }
     const int saved_tb = ctx->tb_override, saved_var = ctx->variant;
     z2_run_params p{};
-    const int S = 6;
+    const int S = 16;  // Trotter steps per timing (shorter samples misranked close candidates)
     p.lambda = 1.0;
     p.T = 0.04 * S;
     p.M = S;

@@ -260,7 +260,7 @@ def test_argument_errors(ctx):
     assert np.allclose(host(g), 2 ** -9)
 
 
-@pytest.mark.parametrize("variant,tile_bits", [(1, 0), (2, 0), (2, 12), (1, 13), (2, 11), (1, 10), (3, 0), (3, 12), (3, 10), (3, 13), (4, 12), (4, 13)])
+@pytest.mark.parametrize("variant,tile_bits", [(1, 0), (2, 0), (2, 12), (1, 13), (2, 11), (1, 10), (3, 0), (3, 12), (3, 10), (3, 13), (4, 12), (4, 13), (5, 12), (5, 13)])
 @pytest.mark.parametrize("d,L", [(2, (3, 3)), (2, (5, 2)), (2, (4, 3)), (3, (2, 2, 2))])
 def test_kernel_variants_and_tilings(ctx, variant, tile_bits, d, L):
     # every execution variant (direct global loads / TMA pipeline) and tile
@@ -295,7 +295,7 @@ def test_autotune_then_parity(ctx, d, L):
     tr = z2.z2_autotune(ctx, lat.handle, z2.Z2_C64, g)
     assert tr.n_candidates >= 1 and tr.us_per_step > 0
     if ol.n_links > 14:
-        assert tr.tile_bits in (12, 13, 14) and tr.variant in (1, 3, 4)
+        assert tr.tile_bits in (12, 13, 14) and tr.variant in (1, 3, 4, 5)
     lam, T, M = 2.0, 1.0, 12
     psi = oracle.run(ol, lam, T, M, 1)
     z2.z2_init_plus(ctx, lat.handle, z2.Z2_C64, g)
@@ -306,7 +306,7 @@ def test_autotune_then_parity(ctx, d, L):
         assert info.tile_bits == tr.tile_bits
 
 
-@pytest.mark.parametrize("variant,tile_bits,low,groups", [(3, 13, 12, 3), (3, 12, 11, 4), (1, 13, 13, 3), (4, 13, 13, 3)])
+@pytest.mark.parametrize("variant,tile_bits,low,groups", [(3, 13, 12, 3), (3, 12, 11, 4), (1, 13, 13, 3), (4, 13, 13, 3), (5, 13, 12, 3)])
 def test_ring_low_group_tile(ctx, variant, tile_bits, low, groups):
     # 32 qubits (4x4): the complex64 ring runs the low group on a tile one bit
     # smaller (twice the workers) when the strided groups absorb the extra bit
