@@ -229,6 +229,29 @@ typedef struct {
 int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, int32_t j0, int32_t j1,
                         z2_plan_info *out);
 
+/* Host-only view of the qubit grouping a plan uses (the streaming passes of
+ * Sec. 2.3's layers, see z2_plan_info): for a state of n_qubits at
+ * `precision`, with tile size `tile_bits` (0 = automatic) and pass variant
+ * `variant` (Z2_OPT_PASS_VARIANT values), writes up to max_groups groups, the
+ * low (contiguous) group first.  Group i rotates global bits [b, b + k1) and,
+ * when k1 < k, also [b2, b2 + k - k1) (a group split in two ranges, the upper
+ * one ending at bit n_qubits - 1); its tiles hold 2^tile_bits amplitudes, the
+ * c lowest global bits followed by the group's bits.  assume_tma != 0 plans as
+ * if the driver's tensor-map encoder were available (the TMA ring plans), so
+ * that the grouping can be inspected on any machine.  Needs no GPU and
+ * allocates nothing on the device.  Errors: Z2_ERR_ARG, Z2_ERR_LATTICE (no
+ * tile size fits). */
+typedef struct {
+    int32_t tile_bits;  /* tile size of this group's passes                     */
+    int32_t c;          /* passenger bits: global bits [0, c) in every tile     */
+    int32_t b;          /* first rotated global bit                             */
+    int32_t k;          /* rotated bits                                         */
+    int32_t k1;         /* rotated bits starting at b (k1 == k: contiguous)     */
+    int32_t b2;         /* start of the upper range when k1 < k, else 0         */
+} z2_group_info;
+int z2_plan_geometry(int32_t n_qubits, int32_t precision, int32_t tile_bits, int32_t variant, int32_t assume_tma,
+                     z2_group_info *groups, int32_t max_groups, int32_t *n_groups);
+
 /* ---- observables (Sec. 2.4) -----------------------------------------------
  * Fills `out` for the state at ramp parameter s (energy = <H(s)>).  `ref` is
  * an optional device state of the same size and precision for the fidelity

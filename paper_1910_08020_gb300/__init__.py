@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "Z2Error", "RunParams", "Results", "LatticeInfo", "load", "build",
     "z2_ctx_create", "z2_ctx_destroy", "z2_last_error", "z2_version", "z2_ctx_launch_count",
-    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_ctx_set_option", "z2_autotune", "TuneResult",
+    "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_plan_geometry", "GroupInfo", "z2_ctx_set_option", "z2_autotune", "TuneResult",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
     "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static",
@@ -66,6 +66,11 @@ class PlanInfo(ctypes.Structure):
                 ("low_tile_bits", ctypes.c_int32)]
 
 
+class GroupInfo(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int32), ("c", ctypes.c_int32), ("b", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("k1", ctypes.c_int32), ("b2", ctypes.c_int32)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int32), ("variant", ctypes.c_int32), ("us_per_step", ctypes.c_double),
                 ("n_candidates", ctypes.c_int32)]
@@ -106,6 +111,7 @@ _SIGS = {
     "z2_ctx_set_option": [_P, _I, _I],
     "z2_autotune": [_P, _P, _I, _P, _P, ctypes.POINTER(TuneResult)],
     "z2_evolve_plan_info": [_P, _P, ctypes.POINTER(RunParams), _I, _I, ctypes.POINTER(PlanInfo)],
+    "z2_plan_geometry": [_I, _I, _I, _I, _I, ctypes.POINTER(GroupInfo), _I, ctypes.POINTER(ctypes.c_int32)],
     "z2_last_error": [_P],
     "z2_version": [],
     "z2_lattice_create": [_I, ctypes.POINTER(_I), ctypes.POINTER(_P)],
@@ -227,6 +233,15 @@ def z2_evolve_plan_info(ctx, lat, params, j0, j1):
     info = PlanInfo()
     _check(load().z2_evolve_plan_info(ctx, lat, ctypes.byref(params), int(j0), int(j1), ctypes.byref(info)), ctx)
     return info
+
+
+def z2_plan_geometry(n_qubits, precision=0, tile_bits=0, variant=0, assume_tma=True):
+    """Qubit groups of a plan (host only, no GPU): list of GroupInfo, low group first."""
+    out = (GroupInfo * 8)()
+    n = ctypes.c_int32(0)
+    _check(load().z2_plan_geometry(int(n_qubits), int(precision), int(tile_bits), int(variant), int(bool(assume_tma)),
+                                   out, 8, ctypes.byref(n)))
+    return [out[i] for i in range(n.value)]
 
 
 def z2_lattice_create(d, L):

@@ -165,12 +165,14 @@ bool tma_possible(bool c128, int tb, int variant) { return variant == 2 && tb <=
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 
 // whether passes of this geometry run on the complex64 TMA ring kernel
-bool ring_plan(bool c128, int variant, int tb, int n_groups) {
+// (tma: the driver's tensor-map encoder is available)
+bool ring_plan(bool c128, int variant, int tb, int n_groups, bool tma) {
     return !c128 && (variant == 3 || variant == 0 || (variant == 5 && tb >= 12)) && n_groups > 1 && tb >= 10 &&
-           tb <= 13 && encode_fn() != nullptr;
+           tb <= 13 && tma;
 }
 
-bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err) {
+bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err,
+                   bool tma = encode_fn() != nullptr) {
     g = Geometry{};
     g.n = n;
     g.c128 = c128;
@@ -231,7 +233,7 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
     // that more than it loses, so it takes the smaller tile whenever the
     // strided groups can absorb the extra bit without an extra pass.
     int tb_low = tb;
-    if (tb >= 11 && ring_plan(c128, variant, tb, h + 1) && n_low == tb) {
+    if (tb >= 11 && ring_plan(c128, variant, tb, h + 1, tma) && n_low == tb) {
         const int rem1 = n - (tb - 1);
         if ((rem1 + kmax(tb) - 1) / kmax(tb) == h && rem1 >= kmin(tb) * h) {
             tb_low = tb - 1;
@@ -272,7 +274,7 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
     // 2 MB pages, and address translation slows the copies down.  Split the
     // pages' bits evenly: one group takes a few bits at the bottom of the
     // strided range and the top ones, the other the middle ones.
-    if (h == 2 && ring_plan(c128, variant, tb, (int)g.groups.size())) {
+    if (h == 2 && ring_plan(c128, variant, tb, (int)g.groups.size(), tma)) {
         constexpr int PAGE_BITS = 18;  // 2 MB / 8 bytes per complex64 amplitude
         auto pages = [&](int lo_, int hi_) { return std::max(0, hi_ - std::max(lo_, PAGE_BITS)); };
         const Group A = g.groups[1], B = g.groups[2];
@@ -511,7 +513,7 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     for (auto &a : P.args) a.p0 = P.gate;
     P.tma = tma_possible(c128, P.geo.tb, P.variant) && encode_fn() != nullptr;
     // the ring variant is the automatic choice for multi-tile complex64 passes
-    P.ring = ring_plan(c128, P.variant, P.geo.tb, (int)P.geo.groups.size());
+    P.ring = ring_plan(c128, P.variant, P.geo.tb, (int)P.geo.groups.size(), encode_fn() != nullptr);
     P.ring_wide = !c128 && P.variant == 4 && P.geo.groups.size() > 1 && P.geo.tb >= 12 && P.geo.tb <= 13 &&
                   encode_fn() != nullptr;
     if (P.ring_wide) P.ring = true;
@@ -942,6 +944,26 @@ int z2_evolve_plan_info(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params 
     out->n_tables = (int)(P->tables.size() / TABLE_STRIDE);
     out->flip = P->flip ? 1 : 0;
     out->low_tile_bits = P->geo.groups.empty() ? 0 : P->geo.groups[0].tb;
+    return Z2_OK;
+}
+
+int z2_plan_geometry(int32_t n_qubits, int32_t precision, int32_t tile_bits, int32_t variant, int32_t assume_tma,
+                     z2_group_info *groups, int32_t max_groups, int32_t *n_groups) {
+    if (!groups || !n_groups) return fail(nullptr, Z2_ERR_ARG, "z2_plan_geometry: NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(nullptr, Z2_ERR_ARG, "bad precision");
+    if (n_qubits < 8 || n_qubits > Z2_MAX_LINKS) return fail(nullptr, Z2_ERR_ARG, "n_qubits must be in 8..34");
+    if (tile_bits != 0 && (tile_bits < 8 || tile_bits > 14)) return fail(nullptr, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
+    if (variant < 0 || variant > 5) return fail(nullptr, Z2_ERR_ARG, "pass variant must be 0..5");
+    z2::Geometry g;
+    std::string err;
+    if (!z2::plan_geometry(n_qubits, precision == Z2_C128, tile_bits, variant, g, err, assume_tma != 0))
+        return fail(nullptr, Z2_ERR_LATTICE, err);
+    if ((int)g.groups.size() > max_groups) return fail(nullptr, Z2_ERR_ARG, "z2_plan_geometry: max_groups too small");
+    for (size_t i = 0; i < g.groups.size(); ++i) {
+        const auto &gr = g.groups[i];
+        groups[i] = z2_group_info{gr.tb, gr.c, gr.b, gr.k, gr.k1, gr.k1 < gr.k ? gr.b2 : 0};
+    }
+    *n_groups = (int32_t)g.groups.size();
     return Z2_OK;
 }
 
