@@ -215,6 +215,8 @@ def run_sweep(args):
     ctx = z2.Context(0)
     if args.variant:
         z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_PASS_VARIANT, args.variant)
+    if getattr(args, "split_low", 0):
+        z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_SPLIT_LOW_BITS, args.split_low)
     specs = workloads.sweep_specs(args.sweep_runs)
     arr = z2.run_specs(specs)
     steps = sum(sp["M"] for sp in specs)
@@ -332,6 +334,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="pass kernel: 0 auto, 1 direct (packed), 2 TMA, 3 ring, 4 ring with 32 pairs per thread, "
                     "5 ring with 32 pairs per thread on the strided groups")
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--split-low", type=int, default=0,
+                    help="ring plans with two strided groups: bits of the split group at the bottom (0 = automatic)")
     ap.add_argument("--autotune", action="store_true",
                     help="time every tile size x kernel variant before the warm-up and run the fastest "
                          "(default: the automatic plan)")
@@ -373,6 +377,8 @@ def main():
     ctx = z2.Context(local)
     if args.variant:
         z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_PASS_VARIANT, args.variant)
+    if getattr(args, "split_low", 0):
+        z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_SPLIT_LOW_BITS, args.split_low)
     if args.tile_bits:
         z2.z2_ctx_set_option(ctx.handle, z2.Z2_OPT_TILE_BITS, args.tile_bits)
     lat = z2.Lattice(wl["d"], wl["L"])

@@ -154,6 +154,10 @@ int z2_ctx_flush_plans(z2_ctx *ctx);
                                  4 = TMA ring with 32 pairs per thread (tile bits 12..13),
                                  5 = TMA ring, strided groups with 32 pairs per thread and
                                      the low group with 16 (tile bits 12..13)               */
+#define Z2_OPT_SPLIT_LOW_BITS 2 /* ring plans with two strided groups: how many of the split
+                                   group's bits sit at the bottom of the strided range (the
+                                   rest at the top); 0 = automatic (share the rotated bits
+                                   below bit 21 evenly between the groups), 1..8 = that many */
 int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
 
 /* Autotuner: times each candidate execution plan of `lat` at `precision`

@@ -212,7 +212,7 @@ def z2_ctx_launch_count(ctx):
     return out.value
 
 
-Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT = 0, 1
+Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT, Z2_OPT_SPLIT_LOW_BITS = 0, 1, 2
 
 
 def z2_ctx_set_option(ctx, option, value):

@@ -110,6 +110,7 @@ struct z2_ctx {
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
     int tb_override = 0;
+    int split_low = 0;  // Z2_OPT_SPLIT_LOW_BITS
     int variant = 0;  // 0 = automatic (ring where it applies, else direct), 1 = direct, 2 = TMA per CTA, 3 = ring,
                       // 4 = ring with 32 pairs per thread
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;  // (qubits, precision) -> (tile bits, variant)
@@ -172,7 +173,7 @@ bool ring_plan(bool c128, int variant, int tb, int n_groups, bool tma) {
 }
 
 bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, std::string &err,
-                   bool tma = encode_fn() != nullptr) {
+                   bool tma = encode_fn() != nullptr, int split_low = 0) {
     g = Geometry{};
     g.n = n;
     g.c128 = c128;
@@ -269,24 +270,40 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         g.groups.push_back(gr);
         lo += k;
     }
-    // Two strided groups on the ring: a tile's rows lie 2^b amplitudes apart,
-    // so each rotated bit at or above PAGE_BITS puts its rows on twice as many
-    // 2 MB pages, and address translation slows the copies down.  Split the
-    // pages' bits evenly: one group takes a few bits at the bottom of the
-    // strided range and the top ones, the other the middle ones.
+    // Two strided groups on the ring: one group takes a few bits at the bottom
+    // of the strided range and the top ones, the other the middle ones.  A
+    // strided pass streams fastest when many of its rotated bits lie below
+    // SPREAD_BITS (rows less than 16 MB apart): measured on a GB300 at 32
+    // qubits (13-bit tiles, two 10-bit groups over bits 12..31), Trotter
+    // steps/s against the split group's bottom bits a = 2..8 were 29.0, 32.2,
+    // 34.2, 34.2, 32.2, 29.0, 29.0, which follows the slower group's share of
+    // the bits 12..20, min(a, 9 - a); a contiguous split (bits 12..21 and
+    // 22..31) ran the upper group at a third more time per pass.  So the bits
+    // below SPREAD_BITS are shared as evenly as the groups allow.
     if (h == 2 && ring_plan(c128, variant, tb, (int)g.groups.size(), tma)) {
-        constexpr int PAGE_BITS = 18;  // 2 MB / 8 bytes per complex64 amplitude
-        auto pages = [&](int lo_, int hi_) { return std::max(0, hi_ - std::max(lo_, PAGE_BITS)); };
+        constexpr int SPREAD_BITS = 21;  // 16 MB / 8 bytes per complex64 amplitude
+        auto spread = [&](int lo_, int hi_) { return std::max(0, std::min(hi_, SPREAD_BITS) - lo_); };
         const Group A = g.groups[1], B = g.groups[2];
         const int base = A.lo;
-        int best = std::max(pages(A.lo, A.hi), pages(B.lo, B.hi)), best_a = -1, best_ks = 0;
+        int best = std::min(spread(A.lo, A.hi), spread(B.lo, B.hi)), best_a = -1, best_ks = 0;
+        if (split_low > 0) {  // requested width of the split group's lower range
+            const int ks = A.k;
+            if (split_low >= ks || split_low > 8 || ks - split_low > 8) {
+                err = "split width " + std::to_string(split_low) + " does not fit a group of " + std::to_string(ks) +
+                      " bits (each range 1..8 bits)";
+                return false;
+            }
+            best_a = split_low;
+            best_ks = ks;
+        }
         for (int ks : {A.k, B.k}) {  // size of the split group
+            if (split_low != 0) break;
             const int km = A.k + B.k - ks;
             for (int a = 1; a < ks && a <= 8; ++a) {
                 if (ks - a > 8) continue;  // each range is one TMA box dimension (<= 256)
                 const int top_lo = n - (ks - a);
-                const int p = std::max(pages(base, base + a) + pages(top_lo, n), pages(base + a, base + a + km));
-                if (p < best) {
+                const int p = std::min(spread(base, base + a) + spread(top_lo, n), spread(base + a, base + a + km));
+                if (p > best) {
                     best = p;
                     best_a = a;
                     best_ks = ks;
@@ -555,7 +572,8 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
     std::string err;
     const auto ch = exec_choice(ctx, lat.n_links, p.precision);
     P.variant = ch.second;
-    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ch.first, ch.second, P.geo, err))
+    if (!plan_geometry(lat.n_links, p.precision == Z2_C128, ch.first, ch.second, P.geo, err,
+                       encode_fn() != nullptr, ctx->split_low))
         return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_RX_TAN;
     if (j1 == j0) return upload_plan(ctx, lat, P);
@@ -689,9 +707,9 @@ std::string plan_key(const z2_ctx *ctx, const char *kind, const Lattice &lat, co
     // the effective tile size and kernel variant are part of the key
     const auto ch = exec_choice(ctx, lat.n_links, p ? p->precision : 0);
     char buf[320];
-    std::snprintf(buf, sizeof(buf), "%s|%d|%d,%d,%d|%a|%a|%d|%d|%d|%d|%d|%d|%a|tb%d|v%d", kind, lat.d, lat.L[0], lat.L[1],
-                  lat.L[2], p ? p->lambda : 0.0, p ? p->T : 0.0, p ? p->M : 0, p ? p->decomp : 0,
-                  p ? p->precision : 0, p ? p->sampling : 0, a, b, x, ch.first, ch.second);
+    std::snprintf(buf, sizeof(buf), "%s|%d|%d,%d,%d|%a|%a|%d|%d|%d|%d|%d|%d|%a|tb%d|v%d|s%d", kind, lat.d, lat.L[0],
+                  lat.L[1], lat.L[2], p ? p->lambda : 0.0, p ? p->T : 0.0, p ? p->M : 0, p ? p->decomp : 0,
+                  p ? p->precision : 0, p ? p->sampling : 0, a, b, x, ch.first, ch.second, ctx->split_low);
     return buf;
 }
 
@@ -721,7 +739,8 @@ int build_hadamard_plan(z2_ctx *ctx, const Lattice &lat, bool c128, Plan &P) {
     std::string err;
     const auto ch = exec_choice(ctx, lat.n_links, c128 ? Z2_C128 : Z2_C64);
     P.variant = ch.second;
-    if (!plan_geometry(lat.n_links, c128, ch.first, ch.second, P.geo, err)) return fail(ctx, Z2_ERR_LATTICE, err);
+    if (!plan_geometry(lat.n_links, c128, ch.first, ch.second, P.geo, err, encode_fn() != nullptr, ctx->split_low))
+        return fail(ctx, Z2_ERR_LATTICE, err);
     P.op = OP_HADAMARD;
     for (int gi = 0; gi < (int)P.geo.groups.size(); ++gi) {
         HostPass hp{};
@@ -840,6 +859,9 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
     if (option == Z2_OPT_TILE_BITS) {
         if (value != 0 && (value < 8 || value > 14)) return fail(ctx, Z2_ERR_ARG, "tile bits must be 0 or 8..14");
         ctx->tb_override = value;
+    } else if (option == Z2_OPT_SPLIT_LOW_BITS) {
+        if (value < 0 || value > 8) return fail(ctx, Z2_ERR_ARG, "split width must be 0 (automatic) or 1..8");
+        ctx->split_low = value;
     } else if (option == Z2_OPT_PASS_VARIANT) {
         if (value < 0 || value > 5) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..5");
         ctx->variant = value;
@@ -1056,7 +1078,8 @@ int z2_apply_plaquettes(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, v
             std::string err;
             const auto ch = exec_choice(ctx, lat->lat.n_links, precision);
             Q.variant = ch.second;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err))
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err,
+                               encode_fn() != nullptr, ctx->split_low))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             push_table(Q, lat->lat, theta, {1, 0});
@@ -1085,7 +1108,8 @@ int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
             std::string err;
             const auto ch = exec_choice(ctx, lat->lat.n_links, precision);
             Q.variant = ch.second;
-            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err))
+            if (!plan_geometry(lat->lat.n_links, precision == Z2_C128, ch.first, ch.second, Q.geo, err,
+                               encode_fn() != nullptr, ctx->split_low))
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             const GateSplit gs = split_gate(dt);

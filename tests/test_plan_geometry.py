@@ -12,7 +12,7 @@ import pytest
 
 import paper_1910_08020_gb300 as z2
 
-PAGE_BITS = 18  # 2 MB pages of 8-byte complex64 amplitudes
+SPREAD_BITS = 21  # rows less than 16 MB (2^21 complex64 amplitudes) apart
 
 
 def rotated_bits(g, low):
@@ -98,12 +98,13 @@ def test_every_grouping_is_consistent(variant, tma):
 
 def test_32_qubit_ring_plan():
     # the benchmark's plan: the low group on a 12-bit tile, the two strided
-    # groups split so that each spans 2^7 pages of a tile
+    # groups split so that they share the nine strided bits below bit 21 as
+    # evenly as they can (4 and 5)
     g = check_plan(32, 13, 5, True)
     got = [(x.tile_bits, x.c, x.b, x.k, x.k1, x.b2) for x in g]
-    assert got == [(12, 12, 12, 12, 12, 0), (13, 3, 12, 10, 3, 25), (13, 3, 15, 10, 10, 0)]
-    pages = [sum(1 for q in rotated_bits(x, False) if q >= PAGE_BITS) for x in g[1:]]
-    assert pages == [7, 7]
+    assert got == [(12, 12, 12, 12, 12, 0), (13, 3, 12, 10, 4, 26), (13, 3, 16, 10, 10, 0)]
+    low = sorted(sum(1 for q in rotated_bits(x, False) if q < SPREAD_BITS) for x in g[1:])
+    assert low == [4, 5]
 
 
 def test_refinements_need_the_ring():
