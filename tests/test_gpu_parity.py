@@ -2,9 +2,10 @@
 oracle, element by element on seeded random states and on the paper's
 workloads (3x3 lattice, 18 qubits; 2x2x2, 24 qubits; 4x3, 24 qubits).
 
-Tolerances (derived in DESIGN.md, "Precision"):
-  complex64 layers: max|gpu - ref| <= 2e-6 * max|ref| per layer (a few
-    rounded FP32 operations per amplitude and qubit)
+Tolerances, from the arithmetic: the state is complex64 with angles, phase
+tables and reductions in FP64, so each layer rounds each amplitude a few
+times in FP32 (about 24 rotation levels x 2^-24 = 1.4e-6 relative):
+  complex64 layers: max|gpu - ref| <= 2e-6 * max|ref| per layer
   complex64 runs: observables |a - b| <= 1e-5 * S, S = 1 for bounded
     observables and N + lambda N_p for the energy; fidelity 1e-6
   complex128: 1e-10 (layers 1e-12)
