@@ -274,6 +274,22 @@ int z2_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *sta
  * for k < n_masks (host arrays), in FP64.  Synchronises `stream`. */
 int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state,
              const uint64_t *masks, int32_t n_masks, double *out, void *stream);
+/* Densities of states (Sec. 3.3, the histograms of the Z and X terms).
+ * Z2_DOS_Z: out[k] = sum of |psi_i|^2 over the basis states with exactly k
+ *   plaquettes of U_p = -1, k = 0..n_plaq (so <sum_p U_p> = sum_k (N_p - 2k)
+ *   out[k]).
+ * Z2_DOS_X: the same in the sigma^x basis, binned by the number w of links
+ *   with sigma^x = -1, w = 0..n_links (X = -sum_l sigma^x_l = 2w - n_links).
+ *   The state is taken to that basis by a Hadamard layer and back (Sec. 2.4),
+ *   so it is unchanged up to rounding.
+ * `out` (host) must hold cap >= n_plaq + 1 (Z) or n_links + 1 (X) doubles;
+ * *n_bins receives the count.  FP64 sums, bit-reproducible for a given size.
+ * Synchronises `stream`.  Errors: Z2_ERR_ARG (NULL, bad kind or precision,
+ * cap too small, unaligned state), Z2_ERR_CUDA, Z2_ERR_DEVICE_TIMEOUT. */
+#define Z2_DOS_Z 0
+#define Z2_DOS_X 1
+int z2_dos(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, int32_t kind, double *out,
+           int32_t cap, int32_t *n_bins, void *stream);
 /* out[0] + i out[1] = <a|b> = sum_i conj(a_i) b_i, FP64.  Synchronises `stream`. */
 int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b,
                double *out, void *stream);

@@ -24,7 +24,8 @@ __all__ = [
     "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_plan_geometry", "GroupInfo", "z2_ctx_set_option", "z2_autotune", "TuneResult",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
-    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static",
+    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static", "z2_dos", "Z2_DOS_Z", "Z2_DOS_X",
+    "trajectory", "finite_differences",
     "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs", "ServeStats",
     "z2_server_create", "z2_server_submit", "z2_server_poll", "z2_server_wait", "z2_server_cancel",
     "z2_server_stats", "z2_server_request_times", "z2_server_destroy",
@@ -111,6 +112,7 @@ _SIGS = {
     "z2_ctx_set_option": [_P, _I, _I],
     "z2_autotune": [_P, _P, _I, _P, _P, ctypes.POINTER(TuneResult)],
     "z2_evolve_plan_info": [_P, _P, ctypes.POINTER(RunParams), _I, _I, ctypes.POINTER(PlanInfo)],
+    "z2_dos": [_P, _P, _I, _P, _I, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(ctypes.c_int32), _P],
     "z2_plan_geometry": [_I, _I, _I, _I, _I, ctypes.POINTER(GroupInfo), _I, ctypes.POINTER(ctypes.c_int32)],
     "z2_last_error": [_P],
     "z2_version": [],
@@ -213,6 +215,7 @@ def z2_ctx_launch_count(ctx):
 
 
 Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT, Z2_OPT_SPLIT_LOW_BITS = 0, 1, 2
+Z2_DOS_Z, Z2_DOS_X = 0, 1
 
 
 def z2_ctx_set_option(ctx, option, value):
@@ -323,6 +326,65 @@ def z2_zsums_static(n_qubits, precision, state, masks, stream=None):
     _check(load().z2_zsums_static(n_qubits, precision, _ptr(state), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                   len(m), out.ctypes.data_as(ctypes.POINTER(_D)), _stream(stream)))
     return out
+
+
+def z2_dos(ctx, lat, precision, state, kind=Z2_DOS_Z, stream=None):
+    """Density of states (Z2_DOS_Z: by plaquettes with U_p = -1; Z2_DOS_X: by
+    links with sigma^x = -1) as a numpy array of n_plaq + 1 or n_links + 1 bins."""
+    out = np.zeros(40, dtype=np.float64)
+    nb = ctypes.c_int32(0)
+    _check(load().z2_dos(ctx, lat, int(precision), _ptr(state), int(kind), out.ctypes.data_as(ctypes.POINTER(_D)),
+                         len(out), ctypes.byref(nb), _stream(stream)), ctx)
+    return out[:nb.value].copy()
+
+
+def trajectory(ctx, lat, p, state, every, ref=None, dos=False, stream=None):
+    """One adiabatic run from |+>^N, measured every `every` Trotter steps and at
+    the end (Sec. 3.2: observables along the ramp, s = j / M).  Built from
+    z2_init_plus, z2_evolve segments and z2_measure (plus z2_dos when `dos`),
+    so every point is the state the unsegmented run has after j steps.
+    `lat` is a Lattice; returns a list of dicts: step j, results (see
+    results_dict) and, with dos, the "zdos" and "xdos" arrays."""
+    if every < 1:
+        raise ValueError("every must be >= 1")
+    marks = list(range(every, p.M, every)) + [p.M]
+    z2_init_plus(ctx, lat.handle, p.precision, state, stream)
+    points, j = [], 0
+    for j1 in marks:
+        z2_evolve(ctx, lat.handle, p, state, j, j1, stream)
+        j = j1
+        point = {"step": j1, **results_dict(z2_measure(ctx, lat.handle, p, state, j1 / p.M, ref, stream), lat.info)}
+        if dos:
+            point["zdos"] = z2_dos(ctx, lat.handle, p.precision, state, Z2_DOS_Z, stream)
+            point["xdos"] = z2_dos(ctx, lat.handle, p.precision, state, Z2_DOS_X, stream)
+        points.append(point)
+    return points
+
+
+def finite_differences(x, y):
+    """First and second derivatives of samples y(x) on an increasing, possibly
+    uneven grid, by three-point differences (second order inside, first order
+    at the two ends for the second derivative): the host step of the paper's
+    critical-point estimate from d<H>/d lambda and d^2<H>/d lambda^2 (Sec. 3.2).
+    Returns (dy, d2y, x at the largest |d2y| inside the grid)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if x.ndim != 1 or x.shape != y.shape or len(x) < 3 or np.any(np.diff(x) <= 0):
+        raise ValueError("need >= 3 samples on a strictly increasing grid")
+    n = len(x)
+    dy = np.empty(n)
+    d2y = np.empty(n)
+    for i in range(n):
+        j = min(max(i, 1), n - 2)  # centre of the three points used
+        h0, h1 = x[j] - x[j - 1], x[j + 1] - x[j]
+        a, b, c = y[j - 1], y[j], y[j + 1]
+        d2 = 2.0 * (h0 * c - (h0 + h1) * b + h1 * a) / (h0 * h1 * (h0 + h1))
+        d1_mid = (h0 * h0 * c + (h1 * h1 - h0 * h0) * b - h1 * h1 * a) / (h0 * h1 * (h0 + h1))
+        dy[i] = d1_mid + d2 * (x[i] - x[j])
+        d2y[i] = d2
+    inner = np.arange(1, n - 1)
+    xc = x[inner[np.argmax(np.abs(d2y[inner]))]]
+    return dy, d2y, xc
 
 
 def z2_overlap(ctx, n_qubits, precision, a, b, stream=None):

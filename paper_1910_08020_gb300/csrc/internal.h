@@ -104,6 +104,11 @@ cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *ma
 cudaError_t launch_overlap(bool c128, const void *a, const void *b, int n, double *partials, double *d_out,
                            cudaStream_t st);
 int max_zsum_masks();
+// density of states over 2^n amplitudes: n_masks >= 1 bins by the number of
+// masks of odd parity (n_masks + 1 bins), n_masks == 0 by popcount (n + 1
+// bins); the bins land in d_out[0 .. *n_bins)
+cudaError_t launch_dos(bool c128, const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
+                       double *d_out, int *n_bins, cudaStream_t st);
 // persistent multi-run evolution (persistent.cu): runs = device array of
 // PersistRun, ctl = zeroed control block, grid = a multiple of persist_gang()
 // no larger than persist_max_ctas(); runs need >= persist_tile_bits() qubits.

@@ -199,6 +199,69 @@ cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *ma
     return cudaGetLastError();
 }
 
+// Density of states (Sec. 3.3): out[k] = sum of |psi_i|^2 over the amplitudes
+// in bin k, where the bin of index i is the number of masks m with
+// popcount(i & m) odd (n_masks >= 1: plaquettes with U_p = -1, the Z density
+// of states), or popcount(i) (n_masks == 0: links with sigma^x = -1 once the
+// state is in the sigma^x basis, the X density of states).  Each thread adds
+// FP64 weights into its own column of shared-memory bins (no atomics); the
+// block then adds each bin's column in a fixed order, and finish_kernel adds
+// the blocks' partials, so results are bit-reproducible for a given size.
+constexpr int DOS_THREADS = 128;
+constexpr int DOS_BINS = 36;        // >= 35 = 34 qubits + 1, >= 33 = 32 masks + 1
+constexpr int DOS_MAX_BLOCKS = 1 << 15;  // DOS_BINS * blocks fits the partials buffer
+
+template <typename C>
+__global__ void __launch_bounds__(DOS_THREADS) dos_kernel(const C *__restrict__ psi, uint64_t per_block,
+                                                          const __grid_constant__ ZMasks zm, int n_masks, int n_bins,
+                                                          double *__restrict__ partials) {
+    __shared__ double bins[DOS_BINS * DOS_THREADS];
+    for (int k = 0; k < DOS_BINS; ++k) bins[k * DOS_THREADS + threadIdx.x] = 0.0;
+    const uint64_t start = (uint64_t)blockIdx.x * per_block;
+    for (uint64_t e = threadIdx.x; e < per_block; e += DOS_THREADS) {
+        const uint64_t i = start + e;
+        const C v = psi[i];
+        const double re = (double)v.x, im = (double)v.y;
+        int k = 0;
+        if (n_masks == 0) {
+            k = __popcll(i);
+        } else {
+#pragma unroll
+            for (int q = 0; q < ZMASKS; ++q)
+                if (q < n_masks) k += __popcll(i & zm.m[q]) & 1;
+        }
+        bins[k * DOS_THREADS + threadIdx.x] += re * re + im * im;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n_bins) {
+        double s = 0;
+        for (int t = 0; t < DOS_THREADS; ++t) s += bins[threadIdx.x * DOS_THREADS + t];
+        partials[(size_t)blockIdx.x * n_bins + threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_dos(bool c128, const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
+                       double *d_out, int *n_bins_out, cudaStream_t st) {
+    if (n < 8 || n > 34 || n_masks < 0 || n_masks > ZMASKS) return cudaErrorInvalidValue;
+    const int n_bins = (n_masks ? n_masks : n) + 1;
+    if (n_bins > DOS_BINS) return cudaErrorInvalidValue;
+    ZMasks zm{};
+    for (int k = 0; k < n_masks; ++k) zm.m[k] = masks[k];
+    const int blocks = reduce_blocks(n) < DOS_MAX_BLOCKS ? reduce_blocks(n) : DOS_MAX_BLOCKS;
+    const uint64_t per_block = (1ull << n) / (uint64_t)blocks;
+    if (c128)
+        dos_kernel<double2><<<blocks, DOS_THREADS, 0, st>>>((const double2 *)state, per_block, zm, n_masks, n_bins,
+                                                            partials);
+    else
+        dos_kernel<float2><<<blocks, DOS_THREADS, 0, st>>>((const float2 *)state, per_block, zm, n_masks, n_bins,
+                                                           partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    finish_kernel<<<n_bins, RED_THREADS, 0, st>>>(partials, blocks, n_bins, d_out);
+    *n_bins_out = n_bins;
+    return cudaGetLastError();
+}
+
 template <typename C>
 __global__ void __launch_bounds__(RED_THREADS) overlap_kernel(const C *__restrict__ a, const C *__restrict__ b,
                                                               uint64_t per_block, double *__restrict__ partials) {

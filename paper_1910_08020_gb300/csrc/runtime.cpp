@@ -1180,6 +1180,38 @@ int z2_zsums(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *state
     return Z2_OK;
 }
 
+int z2_dos(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, int32_t kind, double *out,
+           int32_t cap, int32_t *n_bins, void *stream) {
+    if (!ctx || !lat || !out || !n_bins) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (kind != Z2_DOS_Z && kind != Z2_DOS_X) return fail(ctx, Z2_ERR_ARG, "kind must be Z2_DOS_Z or Z2_DOS_X");
+    if (int rc = check_state(ctx, state)) return rc;
+    const Lattice &L = lat->lat;
+    const int n = L.n_links;
+    const int want = (kind == Z2_DOS_Z ? L.n_plaq : n) + 1;
+    if (cap < want) return fail(ctx, Z2_ERR_ARG, "z2_dos: out holds " + std::to_string(cap) + " bins, needs " +
+                                                     std::to_string(want));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool c128 = precision == Z2_C128;
+    int nb = 0;
+    if (kind == Z2_DOS_Z) {
+        Z2_CUDA(ctx, launch_dos(c128, state, n, L.plaq.data(), (int)L.plaq.size(), ctx->d_partials, ctx->d_out, &nb,
+                                st));
+        ctx->launches += 2;
+    } else {
+        // to the sigma^x basis and back (Sec. 2.4, H sigma^z H = sigma^x)
+        if (int rc = z2_apply_hadamard(ctx, lat, precision, state, st)) return rc;
+        Z2_CUDA(ctx, launch_dos(c128, state, n, nullptr, 0, ctx->d_partials, ctx->d_out, &nb, st));
+        ctx->launches += 2;
+        if (int rc = z2_apply_hadamard(ctx, lat, precision, state, st)) return rc;
+    }
+    Z2_CUDA(ctx, cudaMemcpyAsync(ctx->h_out, ctx->d_out, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    std::memcpy(out, ctx->h_out, nb * sizeof(double));
+    *n_bins = nb;
+    return check_device_error(ctx);
+}
+
 int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b, double *out,
                void *stream) {
     if (!ctx || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
