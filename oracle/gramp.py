@@ -80,3 +80,37 @@ def energy(lat: Lattice, psi, g):
     z = -float(np.sum(zsums(psi, lat.plaq_masks()))) / nrm
     x = -float(np.sum(xsums(psi, [1 << l for l in range(lat.n_links)]).real)) / nrm
     return z + g * x
+
+
+def _apply_w(psi, lat: Lattice, flips):
+    """prod_{mu in flips} W_mu psi, W_mu = prod of sigma^z along the
+    non-contractible loop C_mu (diagonal, +-1)."""
+    n = lat.n_links
+    idx = np.arange(1 << n, dtype=np.uint64)
+    w = lat.w_masks()
+    out = psi.copy()
+    for mu in flips:
+        out = out * (1 - 2 * (_popcount(idx & np.uint64(w[mu])) & 1).astype(np.float64))
+    return out
+
+
+def sector_start(lat: Lattice, flips, start=None) -> np.ndarray:
+    """A degenerate ground state of Z in another topological sector (Sec. 2.4):
+    W_mu applied to the projected start (init_projected(lat), or `start` if
+    given) for every mu in `flips`.  W_mu anticommutes with the 't Hooft
+    operators V_nu whose surface its loop crosses, so their eigenvalues flip
+    from +1 to -1."""
+    return _apply_w(init_projected(lat) if start is None else start, lat, flips)
+
+
+def sector_ground_state(lat: Lattice, g, flips, tol=1e-12):
+    """Lowest state of H(g) = Z + gX in the sector of sector_start(lat, flips)
+    (Sec. 4.3's E(V_x, V_y, ...)).  H(g) = g (-sum sigma^x - (1/g) sum U_p), so
+    this is the Lanczos ground state of the main path's H at s*lambda = 1/g,
+    seeded with prod W_mu |+>^N, which lies in that sector (H keeps V_mu and G_s).
+    Returns (energy of H(g), state, residual)."""
+    from .ed import SparseH, lanczos_ground_state
+    n = lat.n_links
+    seed = _apply_w(np.full(1 << n, 2.0 ** (-n / 2)), lat, flips)
+    E, phi, r = lanczos_ground_state(SparseH(lat, 1.0 / g), seed.real, tol=tol)
+    return g * E, phi.astype(np.complex128), r
