@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,14 @@ struct Lattice {
 bool build_lattice(int d, const int32_t *L, Lattice &out, std::string &err);
 // Record `msg` as this thread's last error (z2_last_error(NULL)); returns code.
 int set_thread_error(int code, const std::string &msg);
+// Bit of the current device in a per-launcher "attributes set" mask:
+// cudaFuncSetAttribute applies to the current device only, so launchers set
+// their shared-memory limit once per device, not once per process.
+inline uint64_t current_device_bit() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return 1ull << (dev & 63);
+}
 
 // ---------------------------------------------------------------------------
 // One fused pass over the state (Sec. 2.2, both layers of a step).

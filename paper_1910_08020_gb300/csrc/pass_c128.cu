@@ -8,12 +8,13 @@ static cudaError_t launch_tb(C *psi, const PassArgs &a, const PassStep *steps, i
                              int grid, cudaStream_t st) {
     using T = Tile<C, TB>;
     const size_t smem = sizeof(C) * T::SMEM_SLOTS;
-    static bool configured = false;  // once per instantiation and process
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel<C, TB, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel<C, TB, OP><<<grid, T::NT, smem, st>>>(psi, a, steps, n_steps, tables);
     return cudaGetLastError();
@@ -48,12 +49,13 @@ static cudaError_t launch_tma_tb(const PassArgs &a, const CUtensorMap &m, const 
                                  const C *tables, int *err, int grid, cudaStream_t st) {
     using T = Tile<C, TB>;
     using TT = TmaTile<C, TB>;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel_tma<C, TB, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)TT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel_tma<C, TB, OP><<<grid, T::NT, TT::SMEM_BYTES, st>>>(a, m, steps, n_steps, tables, err);
     return cudaGetLastError();

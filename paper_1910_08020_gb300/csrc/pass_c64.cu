@@ -13,12 +13,13 @@ static cudaError_t launch_packed_tb(float2 *psi, const PassArgs &a, const PassSt
                                     const float2 *tables, int fmt, int grid, cudaStream_t st) {
     using T = PTile<TB, PACK_W>;
     const size_t smem = sizeof(ulonglong2) * T::SLOTS;
-    static bool configured = false;  // once per instantiation and process
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel_packed<TB, PACK_W, OP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel_packed<TB, PACK_W, OP><<<grid, T::NT, smem, st>>>(psi, a, steps, n_steps, tables, fmt);
     return cudaGetLastError();
@@ -55,12 +56,13 @@ static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const
                                   const float2 *tables, int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, PACK_W>;
     using RT = RingTile<TB, PACK_W>;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP, S8>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel_ring<TB, PACK_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
                                                                                       err);
@@ -105,12 +107,13 @@ static cudaError_t launch_tma_tb(const PassArgs &a, const CUtensorMap &m, const 
                                  const C *tables, int *err, int grid, cudaStream_t st) {
     using T = Tile<C, TB>;
     using TT = TmaTile<C, TB>;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel_tma<C, TB, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)TT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel_tma<C, TB, OP><<<grid, T::NT, TT::SMEM_BYTES, st>>>(a, m, steps, n_steps, tables, err);
     return cudaGetLastError();

@@ -17,12 +17,13 @@ cudaError_t launch_ring5_tb(const PassArgs &a, const CUtensorMap &m, const PassS
                             int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, RING5_W>;
     using RT = RingTile<TB, RING5_W>;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, RING5_W, OP, S8>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     pass_kernel_ring<TB, RING5_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
                                                                                         err);

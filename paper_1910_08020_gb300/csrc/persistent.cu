@@ -193,12 +193,13 @@ size_t persist_ctl_bytes() { return sizeof(PersistCtl); }
 cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st) {
     using T = PTile<PERSIST_TB, PERSIST_W>;
     const size_t smem = sizeof(ulonglong2) * T::SLOTS;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    const uint64_t dev_bit = current_device_bit();
+    if (!(configured.load() & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(persistent_kernel<OP_RX_TAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     // cooperative launch: every CTA is resident at once (or the launch fails),
     // which the gang barriers rely on
