@@ -133,3 +133,23 @@ def test_rejects_bad_ramps():
     for args in ((0.1, 1.0, 3, 0), (0.1, 1.0, 3, 4, SYMMETRIC, 2, 1), (0.1, 1.0, 3, 4, 7)):
         with pytest.raises(ValueError):
             gramp.evolve_gramp(psi.copy(), lat, *args)
+
+
+@pytest.mark.parametrize("d,L", [(2, (2, 2)), (2, (3, 3)), (3, (2, 2, 2))])
+def test_start_state_from_the_span_of_the_plaquette_masks(d, L):
+    # a Hadamard layer maps prod_p (1 + U_p)/2 |+> to prod_p (1 + X_p)/2 |0>: the
+    # uniform superposition over the GF(2) span of the plaquette masks (the
+    # construction planned for the device), so the two must agree
+    lat = Lattice(d, L)
+    n = lat.n_links
+    span = {0}
+    for m in lat.plaq_masks():
+        span |= {v ^ int(m) for v in span}
+    r = len(span).bit_length() - 1
+    assert len(span) == 1 << r
+    if d == 2:
+        assert r == lat.n_plaq - 1  # one dependency among the plaquettes of a torus
+    phi = np.zeros(1 << n, dtype=np.complex128)
+    phi[sorted(span)] = 2.0 ** (-r / 2)
+    oracle.apply_hadamard_all(phi)
+    assert np.max(np.abs(phi - gramp.init_projected(lat))) < 1e-12
