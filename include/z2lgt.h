@@ -110,7 +110,8 @@ typedef struct {
  * entries. */
 typedef struct {
     double s;                       /* ramp parameter the energy refers to         */
-    double energy;                  /* <H(s)> = -sum<sigma^x_l> - s lambda sum<U_p> */
+    double energy;                  /* <H(s)> = -sum<sigma^x_l> - s lambda sum<U_p>
+                                       (the z2_*_gramp calls: <H(g)>, see there)  */
     double norm;                    /* <psi|psi>                                   */
     double mean_plaq;               /* mean <U_p>                                  */
     double wilson_2x2;              /* <W> of the 2x2 loop (NaN if degenerate)     */
@@ -158,6 +159,12 @@ int z2_ctx_flush_plans(z2_ctx *ctx);
                                    group's bits sit at the bottom of the strided range (the
                                    rest at the top); 0 = automatic (share the rotated bits
                                    below bit 21 evenly between the groups), 1..8 = that many */
+#define Z2_OPT_GANG_WAIT_POLLS 3 /* Z2_SWEEP_PERSISTENT: polls of a gang barrier (a counter in
+                                    global memory) before the kernel gives up, sets the device
+                                    error flag and returns, so the call reports
+                                    Z2_ERR_DEVICE_TIMEOUT; 0 = the default (2^26 polls with a
+                                    short sleep each).  A small value makes the bounded wait
+                                    run out on purpose, to exercise the error path. */
 int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value);
 
 /* Autotuner: times each candidate execution plan of `lat` at `precision`
@@ -294,6 +301,99 @@ int z2_dos(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, void *state, i
 int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, const void *b,
                double *out, void *stream);
 
+/* ---- the paper's own schedule (Sec. 2.2-2.4, Sec. 4.3) ---------------------
+ * The paper ramps H(g) = Z + g X, Z = -sum_p U_p, X = -sum_l sigma^x_l, from
+ * g = 0 upward, starting in the ground state of Z.  The ramp has N_s steps of
+ * n substeps; substep m of step k runs for t_s / n at
+ * g_{k,m} = (k - 1) g_s + m g_s / n (Sec. 2.2), split as
+ * exp(-i Z t_s/n) exp(-i g X t_s/n) (Z2_FIRST_ORDER: the paper's asymmetric
+ * split, Eq. (a), the X factor acting first) or exp(-i Z t_s/2n)
+ * exp(-i g X t_s/n) exp(-i Z t_s/2n) (Z2_SYMMETRIC, Eq. (s)).  The same fused
+ * passes as z2_evolve run it: the plaquette angle is fixed and every
+ * transverse-field layer has its own angle g_{k,m} t_s / n.  Caller-owned. */
+typedef struct {
+    double g_s;        /* increase of g per step                          */
+    double t_s;        /* time per step                                   */
+    int32_t N_s;       /* steps, >= 1 (N_s * n <= 2^24)                   */
+    int32_t n;         /* substeps per step, >= 1                         */
+    int32_t decomp;    /* Z2_FIRST_ORDER (Eq. a) or Z2_SYMMETRIC (Eq. s)  */
+    int32_t precision; /* Z2_C64 or Z2_C128                               */
+} z2_gramp_params;
+
+/* The start state of Sec. 2.4: prod_p P_p |+>^N normalised, P_p = (1 + U_p)/2,
+ * i.e. the equal superposition of every link configuration with all U_p = +1
+ * (the ground state of Z, with G_s = V_mu = +1), multiplied by W_mu for every
+ * bit mu set in `sectors` (bit 0 = x, 1 = y, 2 = z): the degenerate ground
+ * state of Z in another topological sector, whose V_nu flip sign where the
+ * loop of W_mu crosses their surface (Sec. 2.4, Sec. 4.3).  Built without a
+ * projection: 2^{-r/2} on the r-dimensional GF(2) span of the plaquette
+ * masks (shifted by the W_mu masks), then the Hadamard layer.  Enqueued on
+ * `stream`.  Z2_ERR_ARG for sector bits >= d. */
+int z2_init_projected(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, uint32_t sectors, void *state,
+                      void *stream);
+/* Steps k0+1 .. k1 of the ramp (0 <= k0 <= k1 <= N_s), in place, enqueued on
+ * `stream`; segments compose: (0, a) then (a, b) equals (0, b). */
+int z2_evolve_gramp(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, void *state, int32_t k0,
+                    int32_t k1, void *stream);
+/* Observables as z2_measure, except out->s = g and
+ * out->energy = <H(g)> = -sum_p <U_p> - g sum_l <sigma^x_l>.  Synchronises
+ * `stream`.  The state is unchanged. */
+int z2_measure_gramp(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, double g, void *state, const void *ref,
+                     void *stream, z2_results *out);
+/* z2_init_projected(sectors), all N_s steps, z2_measure_gramp at g = N_s g_s. */
+int z2_run_gramp(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, uint32_t sectors, void *state,
+                 const void *ref, void *stream, z2_results *out);
+
+/* ---- gate-level circuits (Sec. 2.3, Eq. (ara), Figs. 3 and 4) --------------
+ * One launch per gate on a state of n_qubits qubits (qubit q = index bit q),
+ * the way the paper's simulator executed its circuits: for a literal
+ * comparison with the fused passes and with the paper's gate counts, not for
+ * speed.  Gates: Z2_GATE_CNOT flips q1 where q0 is 1; Z2_GATE_RZ is
+ * R_z(angle) = exp(-i angle sigma^z / 2) on q0; Z2_GATE_RX is
+ * R_x(angle) = exp(-i angle sigma^x / 2) on q0; Z2_GATE_H is the Hadamard
+ * gate on q0 (angle ignored).  Enqueued on `stream`. */
+#define Z2_GATE_CNOT 0
+#define Z2_GATE_RZ 1
+#define Z2_GATE_RX 2
+#define Z2_GATE_H 3
+int z2_apply_gate(z2_ctx *ctx, int32_t n_qubits, int32_t precision, void *state, int32_t kind, int32_t q0,
+                  int32_t q1, double angle, void *stream);
+/* Steps k0+1 .. k1 of the paper's ramp (z2_gramp_params) gate by gate, on a
+ * state of N + 1 qubits whose top qubit (bit N) is the ancilla, in |0>.
+ * Every substep applies, in the paper's order, the transverse-field factor as
+ * N single-link gates R_x(-2 g_{k,m} t_s / n) and each plaquette factor
+ * exp(-i Z_p tau) as the ancilla circuit of Eq. (ara): a CNOT from each of its
+ * four links onto the ancilla, R_z(-2 tau) on the ancilla, the four CNOTs
+ * again in reverse order (9 gates; tau = t_s/n, or t_s/2n twice in the
+ * symmetric split, unmerged).  The ancilla returns to |0>, so the links' half
+ * of the state equals what z2_evolve_gramp gives.  *n_gates (optional) = the
+ * gates applied: (k1 - k0) n (N + 9 N_p) first order, (k1 - k0) n (N + 18 N_p)
+ * symmetric.  Enqueued on `stream`. */
+int z2_evolve_gramp_circuit(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, void *state, int32_t k0,
+                            int32_t k1, void *stream, uint64_t *n_gates);
+
+/* ---- phase estimation (Sec. 2.4, Eq. (leap), Fig. 5) ------------------------
+ * The controlled evolution U(t) = |0><0| (x) exp(-iHt) + |1><1| (x) exp(iHt)
+ * for H = Z + g X at fixed g, with exp(-iHt) by n Trotter steps of t/n,
+ * (exp(-i Z t/n) exp(-i g X t/n))^n (Z2_FIRST_ORDER) or
+ * (exp(-i Z t/2n) exp(-i g X t/n) exp(-i Z t/2n))^n (Z2_SYMMETRIC).  The
+ * control is an ancilla that chooses the direction of time.  Caller-owned. */
+typedef struct {
+    double g;          /* transverse coupling, fixed                      */
+    double t;          /* evolution time of the |0> branch (-t for |1>)   */
+    int32_t n;         /* Trotter steps, 1 .. 2^24                        */
+    int32_t decomp;    /* Z2_FIRST_ORDER or Z2_SYMMETRIC                  */
+    int32_t precision; /* Z2_C64 or Z2_C128                               */
+    int32_t reserved;  /* 0                                               */
+} z2_qpe_params;
+/* U(t) in place on a state of N + 1 qubits whose top qubit (bit N) is the
+ * control: its first 2^N amplitudes (control |0>) evolve for +t, the next
+ * 2^N for -t, each with the fused passes of z2_evolve.  For an eigenstate
+ * |u> of H, (|0> + |1>)|u>/sqrt(2) becomes (e^{-iEt}|0> + e^{iEt}|1>)|u>/sqrt(2):
+ * z2_overlap of the two halves (n_qubits = N) then reads e^{2iEt}/2.
+ * Enqueued on `stream`. */
+int z2_controlled_evolution(z2_ctx *ctx, const z2_lattice *lat, const z2_qpe_params *qp, void *state, void *stream);
+
 /* ---- allocation-free reduction ----------------------------------------------
  * The paper has no counterpart to this call: it serves callers that cannot
  * allocate device memory (a process under a hard memory cap, a plug-in that
@@ -303,10 +403,14 @@ int z2_overlap(z2_ctx *ctx, int32_t n_qubits, int32_t precision, const void *a, 
  * sums and 32 results, doubles), held on every GPU that loads the library
  * until the process exits.  Limits: 1 <= n_masks <= 32 (larger counts return
  * Z2_ERR_ARG with a message in z2_last_error(NULL)), 8 <= n_qubits <= 34.
- * Per-thread sums are carried in FP64, so results agree with z2_zsums to
- * rounding.  The first call on a device looks up the array's device address
- * (do it before any stream capture).  All calls share the array: calls that
- * overlap on the GPU race.  Synchronises `stream`; results in out[0..n_masks). */
+ * Each thread sums runs of 16 amplitudes in the state's precision and adds
+ * each run into FP64; everything after that (warps, blocks, the final sum) is
+ * FP64.  z2_zsums adds in another order, so the two agree within 1e-6
+ * (complex64) or 1e-12 (complex128), not bit for bit.  The first call on a
+ * device (and again after the device's context changes, e.g. after
+ * cudaDeviceReset) looks up the array's device address: make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU race.  Synchronises `stream`; results in out[0..n_masks). */
 int z2_zsums_static(int32_t n_qubits, int32_t precision, const void *state, const uint64_t *masks, int32_t n_masks,
                     double *out, void *stream);
 
@@ -365,6 +469,11 @@ int z2_server_stats(z2_server *srv, z2_serve_stats *out);
 /* Seconds a finished run waited for admission and spent running (host
  * monotonic clock, submit -> admission -> completion seen by the worker). */
 int z2_server_request_times(z2_server *srv, uint64_t ticket, double *queued_s, double *run_s);
+/* Device-clock timestamps of a finished run, in seconds since the server was
+ * created (CUDA events on the run's stream): *first_s once its first kernel
+ * (the |+> initialisation) has run, *end_s once its last work has.  Two runs
+ * whose intervals intersect had work on the GPU at the same time. */
+int z2_server_request_device_times(z2_server *srv, uint64_t ticket, double *first_s, double *end_s);
 /* Stop the worker after the runs already admitted finish; queued runs are
  * cancelled; frees everything. */
 int z2_server_destroy(z2_server *srv);

@@ -24,11 +24,13 @@ __all__ = [
     "z2_ctx_flush_plans", "z2_evolve_plan_info", "PlanInfo", "z2_plan_geometry", "GroupInfo", "z2_ctx_set_option", "z2_autotune", "TuneResult",
     "z2_lattice_create", "z2_lattice_destroy", "z2_lattice_info_get", "z2_lattice_masks", "z2_state_bytes",
     "z2_init_plus", "z2_apply_plaquettes", "z2_apply_rx_layer", "z2_apply_hadamard",
-    "z2_evolve", "z2_measure", "z2_run", "z2_zsums", "z2_overlap", "z2_zsums_static", "z2_dos", "Z2_DOS_Z", "Z2_DOS_X",
+    "z2_evolve", "z2_measure", "z2_run", "GrampParams", "gramp_params", "z2_init_projected", "z2_evolve_gramp",
+    "z2_measure_gramp", "z2_run_gramp", "z2_apply_gate", "z2_evolve_gramp_circuit", "QpeParams", "qpe_params",
+    "z2_controlled_evolution", "z2_zsums", "z2_overlap", "z2_zsums_static", "z2_dos", "Z2_DOS_Z", "Z2_DOS_X",
     "trajectory", "finite_differences",
     "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs", "ServeStats",
     "z2_server_create", "z2_server_submit", "z2_server_poll", "z2_server_wait", "z2_server_cancel",
-    "z2_server_stats", "z2_server_request_times", "z2_server_destroy",
+    "z2_server_stats", "z2_server_request_times", "z2_server_request_device_times", "z2_server_destroy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,6 +56,19 @@ class Z2Error(RuntimeError):
 class RunParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("T", ctypes.c_double), ("M", ctypes.c_int32),
                 ("decomp", ctypes.c_int32), ("precision", ctypes.c_int32), ("sampling", ctypes.c_int32)]
+
+
+class GrampParams(ctypes.Structure):
+    _fields_ = [("g_s", ctypes.c_double), ("t_s", ctypes.c_double), ("N_s", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("decomp", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class QpeParams(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("t", ctypes.c_double), ("n", ctypes.c_int32), ("decomp", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+Z2_GATE_CNOT, Z2_GATE_RZ, Z2_GATE_RX, Z2_GATE_H = 0, 1, 2, 3
 
 
 class LatticeInfo(ctypes.Structure):
@@ -128,6 +143,13 @@ _SIGS = {
     "z2_evolve": [_P, _P, ctypes.POINTER(RunParams), _P, _I, _I, _P],
     "z2_measure": [_P, _P, ctypes.POINTER(RunParams), _P, _D, _P, _P, ctypes.POINTER(Results)],
     "z2_run": [_P, _P, ctypes.POINTER(RunParams), _P, _P, _P, ctypes.POINTER(Results)],
+    "z2_init_projected": [_P, _P, _I, ctypes.c_uint32, _P, _P],
+    "z2_evolve_gramp": [_P, _P, ctypes.POINTER(GrampParams), _P, _I, _I, _P],
+    "z2_measure_gramp": [_P, _P, _I, _D, _P, _P, _P, ctypes.POINTER(Results)],
+    "z2_run_gramp": [_P, _P, ctypes.POINTER(GrampParams), ctypes.c_uint32, _P, _P, _P, ctypes.POINTER(Results)],
+    "z2_apply_gate": [_P, _I, _I, _P, _I, _I, _I, _D, _P],
+    "z2_evolve_gramp_circuit": [_P, _P, ctypes.POINTER(GrampParams), _P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64)],
+    "z2_controlled_evolution": [_P, _P, ctypes.POINTER(QpeParams), _P, _P],
     "z2_zsums": [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_uint64), _I, ctypes.POINTER(_D), _P],
     "z2_overlap": [_P, _I, _I, _P, _P, ctypes.POINTER(_D), _P],
     "z2_sweep": [_P, ctypes.POINTER(RunSpec), _I, _I, _I, ctypes.POINTER(Results)],
@@ -139,6 +161,7 @@ _SIGS = {
     "z2_server_cancel": [_P, ctypes.c_uint64],
     "z2_server_stats": [_P, ctypes.POINTER(ServeStats)],
     "z2_server_request_times": [_P, ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "z2_server_request_device_times": [_P, ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "z2_server_destroy": [_P],
 }
 
@@ -214,7 +237,7 @@ def z2_ctx_launch_count(ctx):
     return out.value
 
 
-Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT, Z2_OPT_SPLIT_LOW_BITS = 0, 1, 2
+Z2_OPT_TILE_BITS, Z2_OPT_PASS_VARIANT, Z2_OPT_SPLIT_LOW_BITS, Z2_OPT_GANG_WAIT_POLLS = 0, 1, 2, 3
 Z2_DOS_Z, Z2_DOS_X = 0, 1
 
 
@@ -309,6 +332,45 @@ def z2_run(ctx, lat, params, state, ref=None, stream=None):
     _check(load().z2_run(ctx, lat, ctypes.byref(params), _ptr(state), _ptr(ref), _stream(stream),
                          ctypes.byref(res)), ctx)
     return res
+
+
+def z2_init_projected(ctx, lat, precision, state, sectors=0, stream=None):
+    _check(load().z2_init_projected(ctx, lat, int(precision), int(sectors), _ptr(state), _stream(stream)), ctx)
+
+
+def z2_evolve_gramp(ctx, lat, gp, state, k0, k1, stream=None):
+    _check(load().z2_evolve_gramp(ctx, lat, ctypes.byref(gp), _ptr(state), int(k0), int(k1), _stream(stream)), ctx)
+
+
+def z2_measure_gramp(ctx, lat, precision, g, state, ref=None, stream=None):
+    res = Results()
+    _check(load().z2_measure_gramp(ctx, lat, int(precision), float(g), _ptr(state), _ptr(ref), _stream(stream),
+                                   ctypes.byref(res)), ctx)
+    return res
+
+
+def z2_run_gramp(ctx, lat, gp, state, sectors=0, ref=None, stream=None):
+    res = Results()
+    _check(load().z2_run_gramp(ctx, lat, ctypes.byref(gp), int(sectors), _ptr(state), _ptr(ref), _stream(stream),
+                               ctypes.byref(res)), ctx)
+    return res
+
+
+def z2_apply_gate(ctx, n_qubits, precision, state, kind, q0, q1=-1, angle=0.0, stream=None):
+    _check(load().z2_apply_gate(ctx, int(n_qubits), int(precision), _ptr(state), int(kind), int(q0), int(q1),
+                                float(angle), _stream(stream)), ctx)
+
+
+def z2_evolve_gramp_circuit(ctx, lat, gp, state, k0, k1, stream=None):
+    """Gate-by-gate ramp on N + 1 qubits (ancilla = top bit); returns the gate count."""
+    n = ctypes.c_uint64(0)
+    _check(load().z2_evolve_gramp_circuit(ctx, lat, ctypes.byref(gp), _ptr(state), int(k0), int(k1),
+                                          _stream(stream), ctypes.byref(n)), ctx)
+    return n.value
+
+
+def z2_controlled_evolution(ctx, lat, qp, state, stream=None):
+    _check(load().z2_controlled_evolution(ctx, lat, ctypes.byref(qp), _ptr(state), _stream(stream)), ctx)
 
 
 def z2_zsums(ctx, n_qubits, precision, state, masks, stream=None):
@@ -463,6 +525,13 @@ def z2_server_request_times(srv, ticket):
     return q.value, r.value
 
 
+def z2_server_request_device_times(srv, ticket):
+    a, b = _D(), _D()
+    _scheck(load().z2_server_request_device_times(srv, ticket, ctypes.byref(a), ctypes.byref(b)),
+            "request device times")
+    return a.value, b.value
+
+
 def z2_server_destroy(srv):
     _scheck(load().z2_server_destroy(srv), "server destroy")
 
@@ -529,6 +598,16 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+def gramp_params(g_s, t_s, N_s, n, decomp=Z2_SYMMETRIC, precision=Z2_C64):
+    """Parameters of the paper's own ramp H(g) = Z + g X (z2_gramp_params)."""
+    return GrampParams(float(g_s), float(t_s), int(N_s), int(n), int(decomp), int(precision))
+
+
+def qpe_params(g, t, n, decomp=Z2_SYMMETRIC, precision=Z2_C64):
+    """Parameters of the controlled evolution U(t) of phase estimation (z2_qpe_params)."""
+    return QpeParams(float(g), float(t), int(n), int(decomp), int(precision), 0)
 
 
 def params(lam, T, M, decomp=Z2_SYMMETRIC, precision=Z2_C64, sampling=Z2_SAMPLE_STD):

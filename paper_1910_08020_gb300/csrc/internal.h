@@ -68,7 +68,7 @@ struct PassArgs {
     uint32_t rot1, rot2;   // rotation masks over tile bits
     int mid;               // MidOp
     int np1;               // n_plaq + 1 (table length)
-    double p0, p1;         // gate parameters: OP_RX_TAN: t = tan(dt); OP_RX_GEN: cos, sin
+    double p0, p1;         // unused (gate values are per pass step)
     double scale;          // MID_SCALE factor
     const void *table;     // device phase table (np1 complex of the state's type)
     int tma_lo_bits;       // tile-id bits below the strided part (b - c of the TMA view)
@@ -105,6 +105,14 @@ int tma_smem_bytes(bool c128, int tb);
 size_t pass_smem(bool c128, int tb);
 cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream_t st);
 cudaError_t launch_flip_all(bool c128, void *state, int n, int grid, cudaStream_t st);
+// one gate (circuit.cu): kind 0 = CNOT(q0 -> q1), 1 = the 2x2 matrix m
+// (row-major, (re, im) pairs) on qubit q0; n = qubits of the state
+cudaError_t launch_gate(bool c128, void *state, int n, int kind, int q0, int q1, const double *m, int grid,
+                        cudaStream_t st);
+// zero the state, then 2^(-r/2) at every index offset ^ (span of basis[0..r)),
+// basis linearly independent over GF(2) (two launches)
+cudaError_t launch_span_state(bool c128, void *state, int n, const uint64_t *basis, int r, uint64_t offset, int grid,
+                              cudaStream_t st);
 // FP64 reductions over 2^n amplitudes (n >= 8): per-block partials in
 // `partials` (reduce_blocks(n) x outputs doubles), then a fixed-order final
 // sum into d_out (device).  zsums: 1 <= n_masks <= max_zsum_masks().
@@ -113,6 +121,7 @@ cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *ma
 cudaError_t launch_overlap(bool c128, const void *a, const void *b, int n, double *partials, double *d_out,
                            cudaStream_t st);
 int max_zsum_masks();
+int zsums_launches(int n, int n_masks);  // kernel launches of one launch_zsums call
 // density of states over 2^n amplitudes: n_masks >= 1 bins by the number of
 // masks of odd parity (n_masks + 1 bins), n_masks == 0 by popcount (n + 1
 // bins); the bins land in d_out[0 .. *n_bins)
@@ -121,7 +130,9 @@ cudaError_t launch_dos(bool c128, const void *state, int n, const uint64_t *mask
 // persistent multi-run evolution (persistent.cu): runs = device array of
 // PersistRun, ctl = zeroed control block, grid = a multiple of persist_gang()
 // no larger than persist_max_ctas(); runs need >= persist_tile_bits() qubits.
-cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st);
+// spin_limit: polls of a gang barrier before it gives up (0 = the default)
+cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st,
+                              uint32_t spin_limit);
 int persist_tile_bits();
 int persist_gang();
 size_t persist_run_bytes();
@@ -139,11 +150,14 @@ struct PersistRunHost {
     int32_t pad;
 };
 int reduce_blocks(int n);
+// size of the partials buffer that every reduction over 2^n amplitudes fits
+size_t reduce_partials_doubles(int n);
 
 struct PassStepHost {
     uint32_t rot1, rot2;
     int32_t mid, table;
     double scale;
+    double g1, g2;  // gate values of the rot1 / rot2 layers
 };
 
 }  // namespace z2

@@ -2,6 +2,7 @@
 // initialisation, the all-qubit sigma^x flip, and the FP64 reductions of
 // Sec. 2.4 (sigma^z-type expectation values and state overlaps).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "pass_kernel.cuh"
@@ -65,6 +66,60 @@ cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream
     return cudaGetLastError();
 }
 
+// Every amplitude zero (the canvas of the projected start state).
+template <typename C>
+__global__ void zero_kernel(C *__restrict__ psi, uint64_t dim) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim; i += (uint64_t)gridDim.x * blockDim.x) {
+        C v;
+        v.x = 0;
+        v.y = 0;
+        psi[i] = v;
+    }
+}
+
+// The uniform superposition over the coset c + span(b_0 .. b_{r-1}) of
+// GF(2)^N: psi[c ^ (xor of b_i over the set bits i of k)] = amp for every
+// k < 2^r.  With linearly independent b_i every k lands on its own index.
+// A Hadamard layer turns the span of the plaquette masks into the projected
+// state prod_p (1 + U_p)/2 |+>^N of Sec. 2.4, and the offset c = w_mu into
+// its topological sector W_mu prod_p (1 + U_p)/2 |+>^N.
+struct SpanBasis {
+    uint64_t b[64];
+};
+
+template <typename C>
+__global__ void span_scatter_kernel(C *__restrict__ psi, const __grid_constant__ SpanBasis B, int r, uint64_t c,
+                                    typename Cfg<C>::real amp) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < (1ull << r);
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t v = c;
+        for (int i = 0; i < r; ++i)
+            if ((k >> i) & 1ull) v ^= B.b[i];
+        C x;
+        x.x = amp;
+        x.y = 0;
+        psi[v] = x;
+    }
+}
+
+cudaError_t launch_span_state(bool c128, void *state, int n, const uint64_t *basis, int r, uint64_t offset, int grid,
+                              cudaStream_t st) {
+    if (r < 0 || r > 63 || r > n) return cudaErrorInvalidValue;
+    SpanBasis B{};
+    for (int i = 0; i < r; ++i) B.b[i] = basis[i];
+    const uint64_t dim = 1ull << n, cnt = 1ull << r;
+    const int zb = (int)std::min<uint64_t>((dim + 255) / 256, (uint64_t)grid);
+    const int sb = (int)std::min<uint64_t>((cnt + 255) / 256, (uint64_t)grid);
+    if (c128) {
+        zero_kernel<double2><<<zb, 256, 0, st>>>((double2 *)state, dim);
+        span_scatter_kernel<double2><<<sb, 256, 0, st>>>((double2 *)state, B, r, offset, exp2(-0.5 * r));
+    } else {
+        zero_kernel<float2><<<zb, 256, 0, st>>>((float2 *)state, dim);
+        span_scatter_kernel<float2><<<sb, 256, 0, st>>>((float2 *)state, B, r, offset, (float)exp2(-0.5 * r));
+    }
+    return cudaGetLastError();
+}
+
 // psi[i] <-> psi[~i]: prod_l sigma^x_l.  It commutes with both layers (every
 // plaquette has four links), so the whole-qubit quarter turns of the gate are
 // collected here once per segment.
@@ -90,17 +145,41 @@ cudaError_t launch_flip_all(bool c128, void *state, int n, int grid, cudaStream_
 }
 
 // ---------------------------------------------------------------------------
-// Reductions.  Each thread sums its amplitudes in the state's precision in
-// short runs (RUN at a time, then into a running sum), a warp combines its 32
-// lanes with shuffles, the block combines its warps in FP64 and writes one
-// FP64 partial per block; a second kernel adds the partials in FP64 in a
-// fixed order, so every result is bit-reproducible for a given launch shape.
+// Reductions.  The sigma^z-type expectation values of Sec. 2.4 are
+// S_k = sum_i |psi_i|^2 (-1)^popcount(i & m_k): for every mask m_k, one
+// coefficient of the Walsh-Hadamard transform of the probabilities.
+//
+// Large states (zsums_wht_kernel): a warp takes chunks of 2^10 amplitudes.
+// Each lane holds 32 probabilities of the chunk (5 index bits in registers, 5
+// bits across the lanes), Walsh-Hadamard transforms them in registers, and
+// leaves the 32 coefficients in shared memory; lane k then forms mask k's
+// coefficient of the chunk as a signed pairwise sum over the 32 lanes' entries
+// (1 + 1 per mask, masks k and k + 32), applies the sign of the chunk's upper
+// index bits, and adds it to an FP64 accumulator.  So each coefficient of a
+// chunk is an FP32 pairwise sum of depth 10 (relative error at most
+// 10 * 2^-24 of the chunk's probability), and everything above one chunk -
+// across chunks, warps, blocks and the final sum - is FP64.  Per amplitude that
+// is about 15 instructions instead of one 64-bit popcount per mask.
+//
+// Small states (zsums_kernel, fewer than 2^13 amplitudes) and overlaps: each
+// thread sums runs of RUN amplitudes in the state's precision and adds each
+// run into an FP64 accumulator; warps combine with FP64 shuffles, blocks in
+// FP64, and a second kernel adds the block partials in FP64 in a fixed order.
+// Every result is bit-reproducible for a given size and device.
 constexpr int RED_THREADS = 256;
-constexpr int ZMASKS = 32;  // masks per zsums launch
+constexpr int ZMASKS = 32;   // masks per zsums_kernel launch
+constexpr int ZW_MASKS = 64; // masks per zsums_wht_kernel launch (two per lane)
 constexpr int RUN = 16;
+constexpr int ZW_WARPS = RED_THREADS / 32;
+constexpr int ZW_CB = 10;    // chunk: 2^10 amplitudes per warp
+constexpr int ZW_LD = 33;    // shared-memory row of one lane's 32 coefficients (padded)
+constexpr int ZW_MAX_BLOCKS = 2048;
 
 struct ZMasks {
     uint64_t m[ZMASKS];
+};
+struct ZMasks64 {
+    uint64_t m[ZW_MASKS];
 };
 
 template <typename C>
@@ -108,7 +187,7 @@ __global__ void __launch_bounds__(RED_THREADS) zsums_kernel(const C *__restrict_
                                                             const __grid_constant__ ZMasks zm, int n_masks,
                                                             double *__restrict__ partials) {
     using real = typename Cfg<C>::real;
-    real acc[ZMASKS];
+    double acc[ZMASKS];
 #pragma unroll
     for (int k = 0; k < ZMASKS; ++k) acc[k] = 0;
     const uint64_t start = (uint64_t)blockIdx.x * per_block;
@@ -131,23 +210,115 @@ __global__ void __launch_bounds__(RED_THREADS) zsums_kernel(const C *__restrict_
             }
         }
 #pragma unroll
-        for (int k = 0; k < ZMASKS; ++k) acc[k] += run[k];
+        for (int k = 0; k < ZMASKS; ++k) acc[k] += (double)run[k];
     }
     __shared__ double wsum[RED_THREADS / 32][ZMASKS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < ZMASKS; ++k) {
         if (k < n_masks) {
-            real v = acc[k];
+            double v = acc[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wsum[warp][k] = (double)v;
+            if (lane == 0) wsum[warp][k] = v;
         }
     }
     __syncthreads();
     if (threadIdx.x < (unsigned)n_masks) {
         double s = 0;
         for (int w = 0; w < RED_THREADS / 32; ++w) s += wsum[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * n_masks + threadIdx.x] = s;
+    }
+}
+
+// Index bits of a chunk: complex64 lanes load 16-byte (two-amplitude) vectors,
+// so chunk offset o = (j & 1) | lane << 1 | (j >> 1) << 6 for register j;
+// complex128: o = lane | j << 5.  u = the mask's register bits (coefficient
+// index in registers), v = its lane bits.
+template <bool C128>
+__device__ __forceinline__ uint32_t zw_u(uint64_t m) {
+    return C128 ? (uint32_t)(m >> 5) & 31u : ((uint32_t)m & 1u) | ((uint32_t)(m >> 6) & 15u) << 1;
+}
+template <bool C128>
+__device__ __forceinline__ uint32_t zw_v(uint64_t m) {
+    return C128 ? (uint32_t)m & 31u : (uint32_t)(m >> 1) & 31u;
+}
+
+// mask coefficient of one chunk: sum over lanes l of (-1)^popc(l & v) row_l[u],
+// pairwise, then the sign of the chunk's upper bits
+template <typename real>
+__device__ __forceinline__ double zw_coeff(const real *sw, uint32_t u, uint32_t v, uint64_t hi_par) {
+    real y[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        const real w = sw[l * ZW_LD + u];
+        y[l] = (__popc((uint32_t)l & v) & 1) ? -w : w;
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < s; ++i) y[i] += y[i + s];
+    const double r = (double)y[0];
+    return (__popcll(hi_par) & 1) ? -r : r;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(RED_THREADS) zsums_wht_kernel(const C *__restrict__ psi, uint64_t n_chunks,
+                                                                const __grid_constant__ ZMasks64 zm, int n_masks,
+                                                                double *__restrict__ partials) {
+    using real = typename Cfg<C>::real;
+    constexpr bool C128 = sizeof(C) == 16;
+    extern __shared__ __align__(16) unsigned char zw_smem[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    real *sw = reinterpret_cast<real *>(zw_smem) + warp * (32 * ZW_LD);
+    const bool has0 = (int)lane < n_masks, has1 = (int)lane + 32 < n_masks;
+    const uint64_t m0 = has0 ? zm.m[lane] : 0, m1 = has1 ? zm.m[lane + 32] : 0;
+    const uint32_t u0 = zw_u<C128>(m0), v0 = zw_v<C128>(m0), u1 = zw_u<C128>(m1), v1 = zw_v<C128>(m1);
+    double acc0 = 0, acc1 = 0;
+    const uint64_t nw = (uint64_t)gridDim.x * ZW_WARPS;
+    for (uint64_t ch = (uint64_t)blockIdx.x * ZW_WARPS + warp; ch < n_chunks; ch += nw) {
+        const uint64_t base = ch << ZW_CB;
+        real x[32];
+        if constexpr (C128) {
+            const C *p = psi + base + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const C v = p[32 * j];
+                x[j] = v.x * v.x + v.y * v.y;
+            }
+        } else {
+            const float4 *p = reinterpret_cast<const float4 *>(psi + base) + lane;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float4 v = p[32 * r];
+                x[2 * r] = v.x * v.x + v.y * v.y;
+                x[2 * r + 1] = v.z * v.z + v.w * v.w;
+            }
+        }
+        // Walsh-Hadamard transform of the lane's 32 probabilities
+#pragma unroll
+        for (int b = 1; b < 32; b <<= 1)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (!(j & b)) {
+                    const real a = x[j], d = x[j | b];
+                    x[j] = a + d;
+                    x[j | b] = a - d;
+                }
+        __syncwarp();  // the previous chunk's rows have been read
+#pragma unroll
+        for (int u = 0; u < 32; ++u) sw[lane * ZW_LD + u] = x[u];
+        __syncwarp();
+        if (has0) acc0 += zw_coeff(sw, u0, v0, base & m0);
+        if (has1) acc1 += zw_coeff(sw, u1, v1, base & m1);
+    }
+    __shared__ double wsum[ZW_WARPS][ZW_MASKS];
+    wsum[warp][lane] = acc0;
+    wsum[warp][lane + 32] = acc1;
+    __syncthreads();
+    if ((int)threadIdx.x < n_masks) {
+        double s = 0;
+        for (int w = 0; w < ZW_WARPS; ++w) s += wsum[w][threadIdx.x];
         partials[(size_t)blockIdx.x * n_masks + threadIdx.x] = s;
     }
 }
@@ -168,11 +339,11 @@ __global__ void __launch_bounds__(RED_THREADS) finish_kernel(const double *__res
     if (threadIdx.x == 0) out[k] = sh[0];
 }
 
-int max_zsum_masks() { return ZMASKS; }
+int max_zsum_masks() { return ZW_MASKS; }
+int zsums_launches(int n, int n_masks) { return n >= ZW_CB + 3 ? 2 : 2 * ((n_masks + ZMASKS - 1) / ZMASKS); }
 
-// Blocks of a reduction over 2^n amplitudes (n >= 8): about 64 amplitudes per
-// thread for n <= 30 (short FP32 runs keep the rounding error of each
-// per-thread sum near 2^-24 relative), at most 2^16 blocks (the size of the
+// Blocks of a run-based reduction over 2^n amplitudes (n >= 8): about 64
+// amplitudes per thread for n <= 30, at most 2^16 blocks (the size of the
 // partials buffer).
 int reduce_blocks(int n) {
     int bpb = n < 14 ? n : 14;
@@ -180,23 +351,83 @@ int reduce_blocks(int n) {
     return 1 << (n - bpb);
 }
 
-cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
-                         double *d_out, cudaStream_t st) {
-    if (n_masks < 1 || n_masks > ZMASKS) return cudaErrorInvalidValue;
-    ZMasks zm{};
-    for (int k = 0; k < n_masks; ++k) zm.m[k] = masks[k];
+// Doubles of partial sums any reduction over 2^n amplitudes may write.
+size_t reduce_partials_doubles(int n) {
+    size_t d = (size_t)reduce_blocks(n) * ZMASKS;
+    if (n >= ZW_CB + 3) {
+        const size_t b = std::min<size_t>(size_t(1) << (n - ZW_CB - 3), ZW_MAX_BLOCKS);
+        d = std::max(d, b * ZW_MASKS);
+    }
+    return d;
+}
+
+// Blocks of zsums_wht_kernel: every SM filled once (a grid-stride loop over
+// the chunks), never more than one block per 8 chunks nor ZW_MAX_BLOCKS.
+template <typename C>
+static int zsums_wht_grid(uint64_t n_chunks, size_t smem) {
+    static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
+    static int per_sm_cache[64] = {};
+    static int sms_cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        if (cudaFuncSetAttribute(zsums_wht_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zsums_wht_kernel<C>, RED_THREADS, smem) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        per_sm_cache[dev & 63] = per_sm < 1 ? 1 : per_sm;
+        sms_cache[dev & 63] = sms;
+        configured |= bit;
+    }
+    const uint64_t full = (uint64_t)per_sm_cache[dev & 63] * sms_cache[dev & 63];
+    uint64_t most = n_chunks / ZW_WARPS < 1 ? 1 : n_chunks / ZW_WARPS;
+    if (most > (uint64_t)ZW_MAX_BLOCKS) most = ZW_MAX_BLOCKS;
+    return (int)(full < most ? full : most);
+}
+
+template <typename C>
+static cudaError_t launch_zsums_t(const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
+                                  double *d_out, cudaStream_t st) {
     const uint64_t dim = 1ull << n;
-    if (n < 8) return cudaErrorInvalidValue;
+    if (n >= ZW_CB + 3) {
+        ZMasks64 zm{};
+        for (int k = 0; k < n_masks; ++k) zm.m[k] = masks[k];
+        const uint64_t n_chunks = dim >> ZW_CB;
+        const size_t smem = sizeof(typename Cfg<C>::real) * ZW_WARPS * 32 * ZW_LD;
+        const int blocks = zsums_wht_grid<C>(n_chunks, smem);
+        if (blocks < 1) return cudaErrorInvalidConfiguration;
+        zsums_wht_kernel<C><<<blocks, RED_THREADS, smem, st>>>((const C *)state, n_chunks, zm, n_masks, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        finish_kernel<<<n_masks, RED_THREADS, 0, st>>>(partials, blocks, n_masks, d_out);
+        return cudaGetLastError();
+    }
     const int blocks = reduce_blocks(n);
     const uint64_t per_block = dim / blocks;
-    if (c128)
-        zsums_kernel<double2><<<blocks, RED_THREADS, 0, st>>>((const double2 *)state, per_block, zm, n_masks, partials);
-    else
-        zsums_kernel<float2><<<blocks, RED_THREADS, 0, st>>>((const float2 *)state, per_block, zm, n_masks, partials);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    finish_kernel<<<n_masks, RED_THREADS, 0, st>>>(partials, blocks, n_masks, d_out);
-    return cudaGetLastError();
+    for (int k0 = 0; k0 < n_masks; k0 += ZMASKS) {
+        const int m = n_masks - k0 < ZMASKS ? n_masks - k0 : ZMASKS;
+        ZMasks zm{};
+        for (int k = 0; k < m; ++k) zm.m[k] = masks[k0 + k];
+        zsums_kernel<C><<<blocks, RED_THREADS, 0, st>>>((const C *)state, per_block, zm, m, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        finish_kernel<<<m, RED_THREADS, 0, st>>>(partials, blocks, m, d_out + k0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_zsums(bool c128, const void *state, int n, const uint64_t *masks, int n_masks, double *partials,
+                         double *d_out, cudaStream_t st) {
+    if (n_masks < 1 || n_masks > ZW_MASKS || n < 8) return cudaErrorInvalidValue;
+    return c128 ? launch_zsums_t<double2>(state, n, masks, n_masks, partials, d_out, st)
+                : launch_zsums_t<float2>(state, n, masks, n_masks, partials, d_out, st);
 }
 
 // Density of states (Sec. 3.3): out[k] = sum of |psi_i|^2 over the amplitudes
@@ -266,7 +497,7 @@ template <typename C>
 __global__ void __launch_bounds__(RED_THREADS) overlap_kernel(const C *__restrict__ a, const C *__restrict__ b,
                                                               uint64_t per_block, double *__restrict__ partials) {
     using real = typename Cfg<C>::real;
-    real sre = 0, sim = 0;
+    double sre = 0, sim = 0;
     const uint64_t start = (uint64_t)blockIdx.x * per_block;
     const uint64_t steps = per_block / RED_THREADS;
     for (uint64_t r = 0; r < steps; r += RUN) {
@@ -279,8 +510,8 @@ __global__ void __launch_bounds__(RED_THREADS) overlap_kernel(const C *__restric
             rre += x.x * y.x + x.y * y.y;
             rim += x.x * y.y - x.y * y.x;
         }
-        sre += rre;
-        sim += rim;
+        sre += (double)rre;
+        sim += (double)rim;
     }
     __shared__ double wsum[RED_THREADS / 32][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -290,8 +521,8 @@ __global__ void __launch_bounds__(RED_THREADS) overlap_kernel(const C *__restric
         sim += __shfl_xor_sync(0xffffffffu, sim, o);
     }
     if (lane == 0) {
-        wsum[warp][0] = (double)sre;
-        wsum[warp][1] = (double)sim;
+        wsum[warp][0] = sre;
+        wsum[warp][1] = sim;
     }
     __syncthreads();
     if (threadIdx.x < 2) {

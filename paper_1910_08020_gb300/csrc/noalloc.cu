@@ -11,9 +11,13 @@
 // The device address of that array is looked up once per device, the first
 // time the entry point runs on it (cudaGetSymbolAddress with that device
 // current); that first call should therefore come before any stream capture.
+// The address is remembered together with the CUDA context it belongs to, and
+// looked up again when the device's current context changes (after a
+// cudaDeviceReset the library's module is loaded anew, at a new address).
 // All calls share the one array: calls that overlap on the GPU (for example
 // on two streams at once) race and give wrong sums.  Each call overwrites
 // every slot it reads, so nothing has to be cleared between calls.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -100,19 +104,45 @@ __global__ void __launch_bounds__(SA_THREADS) zsums_static_finish(const double *
 
 std::mutex g_setup_mu;
 double *g_scratch_ptr[SA_DEVICES] = {};
+CUcontext g_scratch_ctx[SA_DEVICES] = {};
 
-// device address of g_scratch on the current device (looked up once per device)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+// the driver's cuCtxGetCurrent, found through the runtime (no link to libcuda)
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+// device address of g_scratch on the current device: looked up once per device
+// and context (a reset device gets a new context and a new address).  Without
+// a current context, or without the driver's cuCtxGetCurrent, it is looked up
+// on every call; the lookup makes the device's primary context current.
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= SA_DEVICES) return cudaErrorInvalidDevice;
+    const CtxGetCurrentFn get = ctx_get_current();
+    CUcontext cur = nullptr;
+    if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || !cur || g_scratch_ctx[dev] != cur) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
+        if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
         g_scratch_ptr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = cur;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;

@@ -48,11 +48,14 @@ struct Cfg<double2> {
     static constexpr int R = 4;  // 16 amplitudes per thread (64 registers)
 };
 
-// One entry of the per-launch pass list (device memory).
+// One entry of the per-launch pass list (device memory).  g1 / g2: the gate
+// value (tan(delta) for OP_RX_TAN) of the rot1 / rot2 layer, so every
+// rotation layer of a run may have its own angle (the g ramp of Sec. 2.2).
 struct PassStep {
     uint32_t rot1, rot2;
     int32_t mid, table;
     double scale;
+    double g1, g2;
 };
 
 __host__ __device__ constexpr int ctz_c(int x) { return (x & 1) ? 0 : 1 + ctz_c(x >> 1); }
@@ -230,7 +233,6 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, Tile<C, TB>::MINB) pass_kerne
     __shared__ C tab[Z2_MAX_PLAQ + 1];
 
     const uint32_t t = threadIdx.x;
-    const real gate = (real)a.p0;
     const int c = a.c, b = a.b;
     const int hib = b + TB - c;  // first global bit above the tile's strided part
     const uint64_t ntiles = 1ull << (a.n - TB);
@@ -265,30 +267,30 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, Tile<C, TB>::MINB) pass_kerne
             }
             // phase 1: layouts 0, 1, ... as needed
             int cur = 0;
-            rotate_in<C, TB, OP>(0, v, st.rot1, gate);
+            rotate_in<C, TB, OP>(0, v, st.rot1, (real)st.g1);
 #pragma unroll
             for (int q = 1; q < T::K; ++q) {
                 if (st.rot1 & T::owned(q)) {
                     relayout_rt<C, TB>(cur, q, v, sm, t);
                     cur = q;
-                    rotate_in<C, TB, OP>(q, v, st.rot1, gate);
+                    rotate_in<C, TB, OP>(q, v, st.rot1, (real)st.g1);
                 }
             }
             mid_in<C, TB>(cur, v, a, st.mid, st.scale, ptile, t, tab);
             // phase 2: the current layout, then the others downwards, end in layout 0
-            rotate_in<C, TB, OP>(cur, v, st.rot2, gate);
+            rotate_in<C, TB, OP>(cur, v, st.rot2, (real)st.g2);
             const int first = cur;
 #pragma unroll
             for (int q = T::K - 1; q >= 1; --q) {
                 if (q != first && (st.rot2 & T::owned(q))) {
                     relayout_rt<C, TB>(cur, q, v, sm, t);
                     cur = q;
-                    rotate_in<C, TB, OP>(q, v, st.rot2, gate);
+                    rotate_in<C, TB, OP>(q, v, st.rot2, (real)st.g2);
                 }
             }
             if (cur != 0) {
                 relayout_rt<C, TB>(cur, 0, v, sm, t);
-                if (first != 0) rotate_in<C, TB, OP>(0, v, st.rot2, gate);
+                if (first != 0) rotate_in<C, TB, OP>(0, v, st.rot2, (real)st.g2);
             }
         }
         // recompute the addresses instead of keeping 2^R pointers live
@@ -395,7 +397,6 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, 1)
     auto buf = [&](int k) { return reinterpret_cast<C *>(base + k * TT::BUF_BYTES); };
 
     const uint32_t t = threadIdx.x;
-    const real gate = (real)a.p0;
     const uint64_t ntiles = 1ull << (a.n - TB);
     const int lo_bits = a.tma_lo_bits;      // tile-id bits below the strided part
     const int c = a.c, b = a.b, hib = b + TB - c;
@@ -459,29 +460,29 @@ __global__ void __launch_bounds__(Tile<C, TB>::NT, 1)
                 __syncthreads();
             }
             int cur_l = 0;
-            rotate_in<C, TB, OP>(0, v, st.rot1, gate);
+            rotate_in<C, TB, OP>(0, v, st.rot1, (real)st.g1);
 #pragma unroll
             for (int q = 1; q < T::K; ++q) {
                 if (st.rot1 & T::owned(q)) {
                     relayout_rt<C, TB>(cur_l, q, v, sm, t);
                     cur_l = q;
-                    rotate_in<C, TB, OP>(q, v, st.rot1, gate);
+                    rotate_in<C, TB, OP>(q, v, st.rot1, (real)st.g1);
                 }
             }
             mid_in<C, TB>(cur_l, v, a, st.mid, st.scale, ptile, t, tab);
-            rotate_in<C, TB, OP>(cur_l, v, st.rot2, gate);
+            rotate_in<C, TB, OP>(cur_l, v, st.rot2, (real)st.g2);
             const int first = cur_l;
 #pragma unroll
             for (int q = T::K - 1; q >= 1; --q) {
                 if (q != first && (st.rot2 & T::owned(q))) {
                     relayout_rt<C, TB>(cur_l, q, v, sm, t);
                     cur_l = q;
-                    rotate_in<C, TB, OP>(q, v, st.rot2, gate);
+                    rotate_in<C, TB, OP>(q, v, st.rot2, (real)st.g2);
                 }
             }
             if (cur_l != 0) {
                 relayout_rt<C, TB>(cur_l, 0, v, sm, t);
-                if (first != 0) rotate_in<C, TB, OP>(0, v, st.rot2, gate);
+                if (first != 0) rotate_in<C, TB, OP>(0, v, st.rot2, (real)st.g2);
             }
         }
         __syncthreads();  // padded reads done before the dense store image is written

@@ -131,6 +131,9 @@ __device__ __forceinline__ void prot(u64 (&re)[1 << W], u64 (&im)[1 << W], uint3
         (void)mt;
 #pragma unroll
         for (int q = 0; q < W; ++q) {
+            // register bits that are not this layout's own bits (the last
+            // layout owns fewer than W) never rotate here: no code for them
+            if (!(((T::ownY(Q) >> T::w0(Q)) >> q) & 1u)) continue;
             const float g = (m & (1u << q)) ? t : 0.0f;
             const u64 tq = pk2(g, g), mq = pk2(-g, -g);
 #pragma unroll
@@ -292,33 +295,53 @@ __device__ __forceinline__ void prelayout_rt(int qa, int qb, u64 (&re)[1 << W], 
 // one pass step on the registers of a tile (layout 0 in and out)
 template <int TB, int W, int OP, bool S8 = false>
 __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, const PassArgs &a,
-                                      float gate, uint32_t ptile, uint32_t t, ulonglong2 *sm, const float *tabr,
+                                      float g1, float g2, uint32_t ptile, uint32_t t, ulonglong2 *sm, const float *tabr,
                                       const float *tabi, int bar) {
     using T = PTile<TB, W>;
     int cur = 0;
-    prot_in<TB, W, OP>(0, re, im, st.rot1, gate);
+    prot_in<TB, W, OP>(0, re, im, st.rot1, g1);
 #pragma unroll
     for (int q = 1; q < T::K; ++q) {
         if ((st.rot1 >> 1) & T::ownY(q)) {
             prelayout_rt<TB, W, S8>(cur, q, re, im, sm, t, bar);
             cur = q;
-            prot_in<TB, W, OP>(q, re, im, st.rot1, gate);
+            prot_in<TB, W, OP>(q, re, im, st.rot1, g1);
         }
     }
     pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
-    prot_in<TB, W, OP>(cur, re, im, cur == 0 ? st.rot2 : (st.rot2 & ~1u), gate);
+    if (st.rot2 == 0) {  // no second rotation (uniform over the launch): back to layout 0
+        if (cur != 0) prelayout_rt<TB, W, S8>(cur, 0, re, im, sm, t, bar);
+        return;
+    }
+    prot_in<TB, W, OP>(cur, re, im, cur == 0 ? st.rot2 : (st.rot2 & ~1u), g2);
     const int first = cur;
 #pragma unroll
     for (int q = T::K - 1; q >= 1; --q) {
         if (q != first && ((st.rot2 >> 1) & T::ownY(q))) {
             prelayout_rt<TB, W, S8>(cur, q, re, im, sm, t, bar);
             cur = q;
-            prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, gate);
+            prot_in<TB, W, OP>(q, re, im, st.rot2 & ~1u, g2);
         }
     }
     if (cur != 0) {
         prelayout_rt<TB, W, S8>(cur, 0, re, im, sm, t, bar);
-        if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, gate);
+        if (first != 0) prot_in<TB, W, OP>(0, re, im, st.rot2, g2);
+    }
+}
+
+// Ask the TMA unit to pull a tile into L2 ahead of its use (no completion is
+// tracked: a prefetch never blocks and never faults on in-range addresses).
+// The tile is 2^(TB-c) rows of 2^c contiguous complex64 amplitudes, row r at
+// global index g0 + (r << b); threads of the CTA share the rows in units of at
+// most 16 KB.
+template <int TB>
+__device__ __forceinline__ void prefetch_tile_l2(const float2 *psi, uint64_t g0, int c, int b, uint32_t t, uint32_t nt) {
+    const int ub = c + 3 < 14 ? c + 3 : 14;  // log2 bytes of one unit
+    const uint32_t units_per_row = 1u << (c + 3 - ub), rows = 1u << (TB - c);
+    for (uint32_t u = t; u < rows * units_per_row; u += nt) {
+        const uint64_t r = u / units_per_row, k = u % units_per_row;
+        const char *addr = reinterpret_cast<const char *>(psi + g0 + (r << b)) + (k << ub);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr), "r"(1u << ub) : "memory");
     }
 }
 
@@ -333,7 +356,6 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
     __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
 
     const uint32_t t = threadIdx.x;
-    const float gate = (float)a.p0;
     const int c = a.c, b = a.b;
     const int hib = b + TB - c;
     const uint64_t ntiles = 1ull << (a.n - TB);
@@ -350,6 +372,11 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
         uint32_t ptile = 0;
         for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
+        // this CTA's next tile streams into L2 while this one is loaded and transformed
+        if (tile + gridDim.x < ntiles) {
+            const uint64_t nx = tile + gridDim.x, nlo = nx & ((1ull << (b - c)) - 1ull);
+            prefetch_tile_l2<TB>(psi, (nlo << c) | ((nx >> (b - c)) << hib), c, b, t, T::NT);
+        }
 
         u64 re[T::NP], im[T::NP];
         {
@@ -381,7 +408,7 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
                 }
                 __syncthreads();
             }
-            pstep<TB, W, OP>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, -1);
+            pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, -1);
         }
         uint64_t off = g0 + gthr;
         asm volatile("" : "+l"(off));
@@ -458,7 +485,6 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
 
     const uint32_t worker = threadIdx.x / T::NT, t = threadIdx.x % T::NT;
     const int bar = 1 + (int)worker;
-    const float gate = (float)a.p0;
     // a group may be split in two bit ranges (see the host planner): the
     // tile-id bits above the lower range start at a.hib, and the TMA view
     // takes them in dimension 3 instead of 4
@@ -550,7 +576,7 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
             }
         }
         tile_sync<T::NT>(bar);  // dense reads done before the padded layouts reuse the buffer
-        pstep<TB, W, OP, S8>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, bar);
+        pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, bar);
         tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
         if (out_split) {
 #pragma unroll

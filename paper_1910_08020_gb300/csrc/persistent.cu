@@ -7,8 +7,9 @@
 // |+> written in place of the first load), splitting each pass's tiles among
 // its CTAs, and meets at a gang barrier between passes.  Gangs never wait on
 // each other, and a gang's CTAs are co-resident, so the barrier always
-// completes; it is still bounded: after MBAR-like limits it sets the error flag
-// and the gang stops.
+// completes; it is still bounded: after a poll limit (2^26 polls by default,
+// lower on request, see Z2_OPT_GANG_WAIT_POLLS) it sets the error flag and the
+// CTA returns; the gang's other CTAs give up at their next barrier.
 #include <cuda_runtime.h>
 
 #include "pass_kernel.cuh"
@@ -40,14 +41,15 @@ struct PersistCtl {
     unsigned long long run_of[64];
 };
 
-__device__ __forceinline__ bool gang_barrier(PersistCtl *ctl, int g, unsigned long long target, int *err) {
+__device__ __forceinline__ bool gang_barrier(PersistCtl *ctl, int g, unsigned long long target, int *err,
+                                             uint32_t spin_limit) {
     __syncthreads();
     __shared__ int ok_s;
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(&ctl->bar[g], 1ull);
         int ok = 0;
-        for (uint32_t k = 0; k < GANG_SPIN_LIMIT; ++k) {
+        for (uint32_t k = 0; k < spin_limit; ++k) {
             unsigned long long v;
             asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&ctl->bar[g]) : "memory");
             if (v >= target) {
@@ -65,7 +67,7 @@ __device__ __forceinline__ bool gang_barrier(PersistCtl *ctl, int g, unsigned lo
 
 template <int OP>
 __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
-    persistent_kernel(const PersistRun *__restrict__ runs, int n_runs, PersistCtl *ctl, int *err) {
+    persistent_kernel(const PersistRun *__restrict__ runs, int n_runs, PersistCtl *ctl, int *err, uint32_t spin_limit) {
     constexpr int TB = PERSIST_TB, W = PERSIST_W;
     using T = PTile<TB, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -79,12 +81,12 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
     unsigned long long epoch = 0;
     for (;;) {
         // the gang leader takes the next run and publishes it to the gang
-        if (!gang_barrier(ctl, g, (++epoch) * GANG, err)) return;
+        if (!gang_barrier(ctl, g, (++epoch) * GANG, err, spin_limit)) return;
         if (rank == 0 && t == 0) {
             ctl->run_of[g] = atomicAdd(&ctl->next_run, 1ull);
             __threadfence();
         }
-        if (!gang_barrier(ctl, g, (++epoch) * GANG, err)) return;
+        if (!gang_barrier(ctl, g, (++epoch) * GANG, err, spin_limit)) return;
         if (t == 0) {
             unsigned long long v;
             asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&ctl->run_of[g]) : "memory");
@@ -107,7 +109,6 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
             }
             __syncthreads();
             const PassArgs &a = a_s;
-            const float gate = (float)a.p0;
             const int c = a.c, b = a.b, hib = b + TB - c;
             const uint32_t x0 = 2u * t;
             const uint64_t gthr = (uint64_t)(x0 & ((1u << c) - 1u)) | ((uint64_t)(c < TB ? (x0 >> c) : 0u) << b);
@@ -121,6 +122,10 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
             for (uint64_t tile = rank; tile < ntiles; tile += GANG) {
                 const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
                 const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
+                if (!first && tile + GANG < ntiles) {  // the next tile into L2 (see prefetch_tile_l2)
+                    const uint64_t nx = tile + GANG, nlo = nx & ((1ull << (b - c)) - 1ull);
+                    prefetch_tile_l2<TB>(R.state, (nlo << c) | ((nx >> (b - c)) << hib), c, b, t, T::NT);
+                }
                 uint32_t ptile = 0;
                 for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
                 u64 re[T::NP], im[T::NP];
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
                         }
                         __syncthreads();
                     }
-                    pstep<TB, W, OP>(re, im, st, a, gate, ptile, t, sm, tabr, tabi, -1);
+                    pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, -1);
                 }
                 float2 *q = R.state + g0 + gthr;
                 if (out_split) {
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
                 __syncthreads();  // the shared scratch is reused by the next tile
             }
             // all tiles of this pass are written before any CTA of the gang reads the next
-            if (!gang_barrier(ctl, g, (++epoch) * GANG, err)) return;
+            if (!gang_barrier(ctl, g, (++epoch) * GANG, err, spin_limit)) return;
         }
     }
 }
@@ -190,7 +195,9 @@ int persist_gang() { return GANG; }
 size_t persist_run_bytes() { return sizeof(PersistRun); }
 size_t persist_ctl_bytes() { return sizeof(PersistCtl); }
 
-cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st) {
+cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err, int grid, cudaStream_t st,
+                              uint32_t spin_limit) {
+    if (spin_limit == 0) spin_limit = GANG_SPIN_LIMIT;
     using T = PTile<PERSIST_TB, PERSIST_W>;
     const size_t smem = sizeof(ulonglong2) * T::SLOTS;
     static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
@@ -205,7 +212,7 @@ cudaError_t launch_persistent(const void *runs, int n_runs, void *ctl, int *err,
     // which the gang barriers rely on
     const PersistRun *r = static_cast<const PersistRun *>(runs);
     PersistCtl *c = static_cast<PersistCtl *>(ctl);
-    void *params[] = {(void *)&r, (void *)&n_runs, (void *)&c, (void *)&err};
+    void *params[] = {(void *)&r, (void *)&n_runs, (void *)&c, (void *)&err, (void *)&spin_limit};
     return cudaLaunchCooperativeKernel((const void *)persistent_kernel<OP_RX_TAN>, dim3(grid), dim3(T::NT), params, smem,
                                        st);
 }

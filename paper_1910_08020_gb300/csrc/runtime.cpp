@@ -80,7 +80,6 @@ struct HostPass {
 struct Plan {
     Geometry geo;
     int op = OP_RX_TAN;
-    double gate = 0;  // tan(delta) for OP_RX_TAN
     std::vector<HostPass> passes;
     std::vector<std::complex<double>> tables;  // n_tables x (Z2_MAX_PLAQ + 1)
     bool flip = false;
@@ -105,7 +104,7 @@ struct z2_ctx {
     int device = 0;
     int sm_count = 0;
     std::string last_error;
-    double *d_partials = nullptr;  // reduction partials (2^16 x 32 doubles)
+    double *d_partials = nullptr;  // reduction partials (reduce_partials_doubles(Z2_MAX_LINKS))
     double *d_out = nullptr;       // reduction outputs (256 doubles)
     double *h_out = nullptr;       // pinned copy of d_out
     std::map<std::string, std::unique_ptr<z2::Plan>> plans;
@@ -116,13 +115,13 @@ struct z2_ctx {
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;  // (qubits, precision) -> (tile bits, variant)
     uint64_t launches = 0;
     int *d_err = nullptr;  // device flag: a bounded wait gave up
+    uint32_t gang_wait_polls = 0;  // Z2_OPT_GANG_WAIT_POLLS (0 = the kernel's default)
 };
 
 namespace z2 {
 namespace {
 
 constexpr int TABLE_STRIDE = Z2_MAX_PLAQ + 1;
-constexpr size_t PARTIALS_DOUBLES = (size_t(1) << 16) * 32;
 constexpr int OUT_DOUBLES = 256;
 
 }  // namespace
@@ -354,7 +353,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
         tried = true;
         cudaDriverEntryPointQueryResult q;
         void *p = nullptr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
@@ -430,6 +429,7 @@ struct Event {
     int kind;  // 0 = group, 1 = D
     int group;
     int table;
+    double gate = 0;  // group events: the gate value (tan(delta)) of this application
 };
 
 void pack_passes(const std::vector<Event> &ev, const Geometry &g, std::vector<HostPass> &out) {
@@ -444,6 +444,7 @@ void pack_passes(const std::vector<Event> &ev, const Geometry &g, std::vector<Ho
             const int gi = ev[i].group;
             p.group = gi;
             p.step.rot1 = g.groups[gi].rot;
+            p.step.g1 = ev[i].gate;
             ++i;
             if (i < ev.size() && ev[i].kind == 1) {
                 p.step.mid = MID_TABLE;
@@ -451,6 +452,7 @@ void pack_passes(const std::vector<Event> &ev, const Geometry &g, std::vector<Ho
                 ++i;
                 if (i < ev.size() && ev[i].kind == 0 && ev[i].group == gi) {
                     p.step.rot2 = g.groups[gi].rot;
+                    p.step.g2 = ev[i].gate;
                     ++i;
                 }
             }
@@ -461,6 +463,7 @@ void pack_passes(const std::vector<Event> &ev, const Geometry &g, std::vector<Ho
             if (i < ev.size() && ev[i].kind == 0) {
                 p.group = ev[i].group;
                 p.step.rot2 = g.groups[p.group].rot;
+                p.step.g2 = ev[i].gate;
                 ++i;
             }
         }
@@ -527,7 +530,6 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
         }
     }
     for (auto &gr : P.geo.groups) P.args.push_back(make_args(lat, P.geo, gr));
-    for (auto &a : P.args) a.p0 = P.gate;
     P.tma = tma_possible(c128, P.geo.tb, P.variant) && encode_fn() != nullptr;
     // the ring variant is the automatic choice for multi-tile complex64 passes
     P.ring = ring_plan(c128, P.variant, P.geo.tb, (int)P.geo.groups.size(), encode_fn() != nullptr);
@@ -578,7 +580,6 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
     P.op = OP_RX_TAN;
     if (j1 == j0) return upload_plan(ctx, lat, P);
     const GateSplit gs = split_gate(p.T / p.M);
-    P.gate = gs.t;
     const auto &g = P.geo;
     std::vector<Event> ev;
     std::complex<double> pending(1, 0);  // gate scale since the last D
@@ -593,7 +594,7 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
         const int G = (int)g.order.size();
         for (int k = 0; k < G; ++k) {
             const int gi = g.order[fwd ? k : G - 1 - k];
-            ev.push_back({0, gi, -1});
+            ev.push_back({0, gi, -1, gs.t});
             const int bits = g.groups[gi].k;
             pending *= std::pow(gs.c, bits) * ipow(gs.q * bits);
         }
@@ -604,6 +605,80 @@ int build_evolve_plan(z2_ctx *ctx, const Lattice &lat, const z2_run_params &p, i
     pack_passes(ev, g, P.passes);
     P.flip = (gs.q & 1) && ((j1 - j0) & 1);
     return upload_plan(ctx, lat, P);
+}
+
+// Plan of substeps J0+1 .. J1 of a fixed-Hamiltonian-form layer sequence:
+// substep j is D(tau) R(a_j) (first order, the R layer acting first) or
+// D(tau/2) R(a_j) D(tau/2) (symmetric), with a_j = angle(j); adjacent half
+// layers D(tau/2) D(tau/2) merge into D(tau).  This is the paper's own ramp
+// (Sec. 2.2, Eqs. a and s) and the fixed-g evolution of phase estimation
+// (Sec. 2.4, Eq. leap): with Z = -sum U_p and X = -sum sigma^x,
+// exp(-i Z tau) = D(tau) and exp(-i g X tau) = R(g tau), so the plaquette
+// angle is constant and every R layer may have its own gate value.
+int build_substep_plan(z2_ctx *ctx, const Lattice &lat, int precision, bool sym, double tau, int64_t J0, int64_t J1,
+                       const std::function<double(int64_t)> &angle, Plan &P) {
+    std::string err;
+    const auto ch = exec_choice(ctx, lat.n_links, precision);
+    P.variant = ch.second;
+    if (!plan_geometry(lat.n_links, precision == Z2_C128, ch.first, ch.second, P.geo, err,
+                       encode_fn() != nullptr, ctx->split_low))
+        return fail(ctx, Z2_ERR_LATTICE, err);
+    P.op = OP_RX_TAN;
+    if (J1 == J0) return upload_plan(ctx, lat, P);
+    const auto &g = P.geo;
+    std::vector<Event> ev;
+    std::complex<double> pending(1, 0);
+    int n_tab = 0, quarter_turns = 0;
+    if (sym) {
+        push_table(P, lat, tau / 2, pending);
+        ev.push_back({1, 0, n_tab++});
+    }
+    const int G = (int)g.order.size();
+    for (int64_t j = J0 + 1; j <= J1; ++j) {
+        const GateSplit gs = split_gate(angle(j));
+        quarter_turns += gs.q;
+        const bool fwd = ((j - 1) & 1) == 0;
+        for (int k = 0; k < G; ++k) {
+            const int gi = g.order[fwd ? k : G - 1 - k];
+            ev.push_back({0, gi, -1, gs.t});
+            const int bits = g.groups[gi].k;
+            pending *= std::pow(gs.c, bits) * ipow(gs.q * bits);
+        }
+        push_table(P, lat, sym && j == J1 ? tau / 2 : tau, pending);
+        pending = {1, 0};
+        ev.push_back({1, 0, n_tab++});
+    }
+    pack_passes(ev, g, P.passes);
+    P.flip = quarter_turns & 1;
+    return upload_plan(ctx, lat, P);
+}
+
+// Steps k0+1 .. k1 of the paper's own ramp H(g) = Z + g X (Sec. 2.2):
+// substep j = (k-1) n + m holds g_j = j g_s / n for tau = t_s / n.
+int build_gramp_plan(z2_ctx *ctx, const Lattice &lat, const z2_gramp_params &gp, int k0, int k1, Plan &P) {
+    const double tau = gp.t_s / gp.n;
+    return build_substep_plan(ctx, lat, gp.precision, gp.decomp == Z2_SYMMETRIC, tau, (int64_t)k0 * gp.n,
+                              (int64_t)k1 * gp.n, [&](int64_t j) { return (double)j * gp.g_s / gp.n * tau; }, P);
+}
+
+// Linearly independent vectors spanning the same GF(2) space as `vs`.
+std::vector<uint64_t> gf2_basis(const std::vector<uint64_t> &vs) {
+    uint64_t piv[64] = {};
+    for (uint64_t v : vs) {
+        for (int b = 63; b >= 0 && v; --b) {
+            if (!((v >> b) & 1ull)) continue;
+            if (!piv[b]) {
+                piv[b] = v;
+                v = 0;
+            } else {
+                v ^= piv[b];
+            }
+        }
+    }
+    std::vector<uint64_t> out;
+    for (int b = 0; b < 64; ++b)
+        if (piv[b]) out.push_back(piv[b]);
+    return out;
 }
 
 int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
@@ -798,7 +873,7 @@ int z2_ctx_create(int device, z2_ctx **out) {
     auto ctx = std::make_unique<z2_ctx>();
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&ctx->d_partials, PARTIALS_DOUBLES * sizeof(double)) != cudaSuccess ||
+    if (cudaMalloc(&ctx->d_partials, reduce_partials_doubles(Z2_MAX_LINKS) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&ctx->d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
         if (ctx->d_partials) cudaFree(ctx->d_partials);
@@ -865,6 +940,10 @@ int z2_ctx_set_option(z2_ctx *ctx, int32_t option, int32_t value) {
     } else if (option == Z2_OPT_PASS_VARIANT) {
         if (value < 0 || value > 5) return fail(ctx, Z2_ERR_ARG, "pass variant must be 0..5");
         ctx->variant = value;
+    } else if (option == Z2_OPT_GANG_WAIT_POLLS) {
+        if (value < 0) return fail(ctx, Z2_ERR_ARG, "gang wait polls must be >= 0 (0 = default)");
+        ctx->gang_wait_polls = (uint32_t)value;
+        return Z2_OK;  // no plan depends on it
     } else {
         return fail(ctx, Z2_ERR_ARG, "unknown option");
     }
@@ -1113,11 +1192,10 @@ int z2_apply_rx_layer(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
                 return fail(ctx, Z2_ERR_LATTICE, err);
             Q.op = OP_RX_TAN;
             const GateSplit gs = split_gate(dt);
-            Q.gate = gs.t;
             std::vector<Event> ev;
             std::complex<double> sc(1, 0);
             for (int gi : Q.geo.order) {
-                ev.push_back({0, gi, -1});
+                ev.push_back({0, gi, -1, gs.t});
                 const int bits = Q.geo.groups[gi].k;
                 sc *= std::pow(gs.c, bits) * ipow(gs.q * bits);
             }
@@ -1146,7 +1224,7 @@ int z2_apply_hadamard(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, voi
 }
 
 struct Scratch {
-    double *d_partials;  // reduction partials (2^16 x 32 doubles for the context's own)
+    double *d_partials;  // reduction partials (reduce_partials_doubles(n) or more)
     double *d_out;       // reduction outputs (OUT_DOUBLES)
     double *h_out;       // pinned copy of d_out
 };
@@ -1159,7 +1237,7 @@ static int zsums_device(z2_ctx *ctx, const Scratch &sc, int n, bool c128, const 
     for (int k = 0; k < n_masks; k += chunk) {
         const int m = std::min(chunk, n_masks - k);
         Z2_CUDA(ctx, launch_zsums(c128, state, n, masks + k, m, sc.d_partials, sc.d_out + out_off + k, st));
-        ctx->launches += 2;
+        ctx->launches += zsums_launches(n, m);
     }
     return Z2_OK;
 }
@@ -1273,7 +1351,10 @@ static int measure_enqueue(z2_ctx *ctx, const z2_lattice *lat, int precision, vo
 }
 
 // Turn the raw sums of measure_enqueue into the results struct.
-static void measure_finish(const Lattice &L, double lambda, double s, const double *h, bool has_ref, z2_results *out) {
+// gform: the energy is the paper's <H(g)> = -sum<U_p> - g sum<sigma^x_l> with
+// g = s (Sec. 2.2), else <H(s)> = -sum<sigma^x_l> - s lambda sum<U_p>.
+static void measure_finish(const Lattice &L, double lambda, double s, const double *h, bool has_ref, z2_results *out,
+                           bool gform = false) {
     const int n = L.n_links, np = L.n_plaq;
     std::vector<uint64_t> zm, xm;
     observable_masks(L, zm, xm);
@@ -1313,7 +1394,7 @@ static void measure_finish(const Lattice &L, double lambda, double s, const doub
     }
     out->mean_star = ss / L.n_sites;
     for (int mu = 0; mu < L.d; ++mu) out->vmu[mu] = h[nz + n + L.n_sites + mu] * inv;
-    out->energy = -sx - s * lambda * sp;
+    out->energy = gform ? -sp - s * sx : -sx - s * lambda * sp;
     if (has_ref) {
         // |<ref|psi>|^2 / (<ref|ref> <psi|psi>)
         const double rn = h[off_fid + 2];
@@ -1350,6 +1431,206 @@ int z2_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params *p, void *sta
 }
 
 // ---------------------------------------------------------------------------
+// The paper's own schedule (Sec. 2.2-2.4): projected start, g ramp.
+
+static int check_gramp(z2_ctx *ctx, const z2_gramp_params *gp) {
+    if (!gp) return fail(ctx, Z2_ERR_ARG, "ramp parameters are NULL");
+    if (gp->N_s < 1 || gp->n < 1) return fail(ctx, Z2_ERR_ARG, "need N_s >= 1 and n >= 1");
+    if ((int64_t)gp->N_s * gp->n > (1 << 24)) return fail(ctx, Z2_ERR_ARG, "N_s * n exceeds 2^24 substeps");
+    if (gp->decomp != Z2_FIRST_ORDER && gp->decomp != Z2_SYMMETRIC) return fail(ctx, Z2_ERR_ARG, "bad decomposition");
+    if (gp->precision != Z2_C64 && gp->precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (!std::isfinite(gp->g_s) || !std::isfinite(gp->t_s)) return fail(ctx, Z2_ERR_ARG, "g_s and t_s must be finite");
+    return Z2_OK;
+}
+
+int z2_init_projected(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, uint32_t sectors, void *state,
+                      void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (int rc = check_state(ctx, state)) return rc;
+    const Lattice &L = lat->lat;
+    if (sectors >> L.d) return fail(ctx, Z2_ERR_ARG, "sector bits beyond the lattice dimension");
+    // H^N prod_p (1 + U_p)/2 |+>^N = prod_p (1 + X_p)/2 |0>: uniform over the
+    // span of the plaquette masks; W_mu = prod sigma^z along its loop becomes
+    // the index shift by w_mu
+    const std::vector<uint64_t> basis = gf2_basis(L.plaq);
+    uint64_t offset = 0;
+    for (int mu = 0; mu < L.d; ++mu)
+        if ((sectors >> mu) & 1u) offset ^= L.wmu[mu];
+    cudaStream_t st = (cudaStream_t)stream;
+    Z2_CUDA(ctx, launch_span_state(precision == Z2_C128, state, L.n_links, basis.data(), (int)basis.size(), offset,
+                                   ctx->sm_count * 16, st));
+    ctx->launches += 2;
+    return z2_apply_hadamard(ctx, lat, precision, state, stream);
+}
+
+int z2_evolve_gramp(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, void *state, int32_t k0, int32_t k1,
+                    void *stream) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_gramp(ctx, gp)) return rc;
+    if (int rc = check_state(ctx, state)) return rc;
+    if (k0 < 0 || k1 > gp->N_s || k0 > k1) return fail(ctx, Z2_ERR_ARG, "need 0 <= k0 <= k1 <= N_s");
+    if (k0 == k1) return Z2_OK;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "|gramp|%a|%a|%d|%d|%d|%d", gp->g_s, gp->t_s, gp->N_s, gp->n, gp->decomp,
+                  gp->precision);
+    z2_run_params pp{};
+    pp.precision = gp->precision;
+    const std::string key = plan_key(ctx, "gramp", lat->lat, &pp, k0, k1, 0) + buf;
+    Plan *P = nullptr;
+    if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) { return build_gramp_plan(ctx, lat->lat, *gp, k0, k1, Q); }))
+        return rc;
+    return exec_plan(ctx, *P, state, (cudaStream_t)stream);
+}
+
+int z2_measure_gramp(z2_ctx *ctx, const z2_lattice *lat, int32_t precision, double g, void *state, const void *ref,
+                     void *stream, z2_results *out) {
+    if (!ctx || !lat || !out) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (!std::isfinite(g)) return fail(ctx, Z2_ERR_ARG, "g must be finite");
+    if (int rc = check_state(ctx, state)) return rc;
+    if (ref)
+        if (int rc = check_state(ctx, ref)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int n_out = 0;
+    if (int rc = measure_enqueue(ctx, lat, precision, state, ref, st, ctx_scratch(ctx), &n_out)) return rc;
+    Z2_CUDA(ctx, cudaStreamSynchronize(st));
+    if (int rc = check_device_error(ctx)) return rc;
+    measure_finish(lat->lat, 0.0, g, ctx->h_out, ref != nullptr, out, true);
+    return Z2_OK;
+}
+
+int z2_run_gramp(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, uint32_t sectors, void *state,
+                 const void *ref, void *stream, z2_results *out) {
+    if (int rc = check_gramp(ctx, gp)) return rc;
+    if (int rc = z2_init_projected(ctx, lat, gp->precision, sectors, state, stream)) return rc;
+    if (int rc = z2_evolve_gramp(ctx, lat, gp, state, 0, gp->N_s, stream)) return rc;
+    return z2_measure_gramp(ctx, lat, gp->precision, gp->N_s * gp->g_s, state, ref, stream, out);
+}
+
+// ---------------------------------------------------------------------------
+// Phase estimation (Sec. 2.4, Eq. leap): U(t) = |0><0| (x) exp(-iHt) +
+// |1><1| (x) exp(iHt) for H = Z + g X at fixed g.  The control qubit is index
+// bit N, so the two halves of the state are the two branches: the first
+// evolves for +t, the second for -t, by the same n-step Trotter formula.
+
+int z2_controlled_evolution(z2_ctx *ctx, const z2_lattice *lat, const z2_qpe_params *qp, void *state, void *stream) {
+    if (!ctx || !lat || !qp) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (qp->n < 1 || qp->n > (1 << 24)) return fail(ctx, Z2_ERR_ARG, "need 1 <= n <= 2^24");
+    if (qp->decomp != Z2_FIRST_ORDER && qp->decomp != Z2_SYMMETRIC) return fail(ctx, Z2_ERR_ARG, "bad decomposition");
+    if (qp->precision != Z2_C64 && qp->precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (!std::isfinite(qp->g) || !std::isfinite(qp->t)) return fail(ctx, Z2_ERR_ARG, "g and t must be finite");
+    if (lat->lat.n_links + 1 > Z2_MAX_LINKS) return fail(ctx, Z2_ERR_LATTICE, "no room for the control qubit");
+    if (int rc = check_state(ctx, state)) return rc;
+    const size_t half_bytes = (size_t)(qp->precision == Z2_C128 ? 16 : 8) << lat->lat.n_links;
+    for (int dir = 0; dir < 2; ++dir) {
+        const double t = dir ? -qp->t : qp->t, tau = t / qp->n, g = qp->g;
+        char buf[200];
+        std::snprintf(buf, sizeof(buf), "|qpe|%a|%a|%d|%d|%d", g, t, qp->n, qp->decomp, qp->precision);
+        z2_run_params pp{};
+        pp.precision = qp->precision;
+        const std::string key = plan_key(ctx, "qpe", lat->lat, &pp, 0, 0, 0) + buf;
+        Plan *P = nullptr;
+        if (int rc = ensure_plan(ctx, key, P, [&](Plan &Q) {
+                return build_substep_plan(ctx, lat->lat, qp->precision, qp->decomp == Z2_SYMMETRIC, tau, 0, qp->n,
+                                          [&](int64_t) { return g * tau; }, Q);
+            }))
+            return rc;
+        void *half = static_cast<char *>(state) + (dir ? half_bytes : 0);
+        if (int rc = exec_plan(ctx, *P, half, (cudaStream_t)stream)) return rc;
+    }
+    return Z2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gate-level execution (Sec. 2.3, Eq. ara, Figs. 3 and 4).
+
+static int gate_matrix(int kind, double angle, double m[8]) {
+    const double c = std::cos(angle / 2), s = std::sin(angle / 2), r = std::sqrt(0.5);
+    switch (kind) {
+        case Z2_GATE_RZ:  // exp(-i angle sigma^z / 2)
+            m[0] = c, m[1] = -s, m[2] = 0, m[3] = 0, m[4] = 0, m[5] = 0, m[6] = c, m[7] = s;
+            return Z2_OK;
+        case Z2_GATE_RX:  // exp(-i angle sigma^x / 2)
+            m[0] = c, m[1] = 0, m[2] = 0, m[3] = -s, m[4] = 0, m[5] = -s, m[6] = c, m[7] = 0;
+            return Z2_OK;
+        case Z2_GATE_H:
+            m[0] = r, m[1] = 0, m[2] = r, m[3] = 0, m[4] = r, m[5] = 0, m[6] = -r, m[7] = 0;
+            return Z2_OK;
+        default:
+            return Z2_ERR_ARG;
+    }
+}
+
+static int enqueue_gate(z2_ctx *ctx, int n, bool c128, void *state, int kind, int q0, int q1, double angle,
+                        cudaStream_t st) {
+    double m[8] = {};
+    if (kind != Z2_GATE_CNOT && gate_matrix(kind, angle, m) != Z2_OK) return fail(ctx, Z2_ERR_ARG, "unknown gate");
+    Z2_CUDA(ctx, launch_gate(c128, state, n, kind == Z2_GATE_CNOT ? 0 : 1, q0, q1, m, ctx->sm_count * 8, st));
+    ctx->launches += 1;
+    return Z2_OK;
+}
+
+int z2_apply_gate(z2_ctx *ctx, int32_t n_qubits, int32_t precision, void *state, int32_t kind, int32_t q0, int32_t q1,
+                  double angle, void *stream) {
+    if (!ctx) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (n_qubits < 2 || n_qubits > Z2_MAX_LINKS + 1) return fail(ctx, Z2_ERR_ARG, "need 2 <= n_qubits <= 35");
+    if (precision != Z2_C64 && precision != Z2_C128) return fail(ctx, Z2_ERR_ARG, "bad precision");
+    if (q0 < 0 || q0 >= n_qubits) return fail(ctx, Z2_ERR_ARG, "qubit out of range");
+    if (kind == Z2_GATE_CNOT && (q1 < 0 || q1 >= n_qubits || q1 == q0))
+        return fail(ctx, Z2_ERR_ARG, "CNOT needs a target qubit other than the control");
+    if (!std::isfinite(angle)) return fail(ctx, Z2_ERR_ARG, "angle must be finite");
+    if (int rc = check_state(ctx, state)) return rc;
+    return enqueue_gate(ctx, n_qubits, precision == Z2_C128, state, kind, q0, q1, angle, (cudaStream_t)stream);
+}
+
+// exp(-i Z tau) = prod_p exp(-i Z_p tau), each plaquette through the ancilla
+// (bit N, in |0>): CNOT from each of its links onto the ancilla, R_z(-2 tau)
+// on the ancilla, the CNOTs again in reverse order (Eq. ara, Fig. 3)
+static int enqueue_plaquettes_circuit(z2_ctx *ctx, const Lattice &L, bool c128, void *state, double tau,
+                                      cudaStream_t st, uint64_t &gates) {
+    const int n = L.n_links + 1, a = L.n_links;
+    for (uint64_t m : L.plaq) {
+        int links[64], k = 0;
+        for (int l = 0; l < L.n_links; ++l)
+            if ((m >> l) & 1ull) links[k++] = l;
+        for (int i = 0; i < k; ++i)
+            if (int rc = enqueue_gate(ctx, n, c128, state, Z2_GATE_CNOT, links[i], a, 0, st)) return rc;
+        if (int rc = enqueue_gate(ctx, n, c128, state, Z2_GATE_RZ, a, -1, -2.0 * tau, st)) return rc;
+        for (int i = k - 1; i >= 0; --i)
+            if (int rc = enqueue_gate(ctx, n, c128, state, Z2_GATE_CNOT, links[i], a, 0, st)) return rc;
+        gates += 2 * k + 1;
+    }
+    return Z2_OK;
+}
+
+int z2_evolve_gramp_circuit(z2_ctx *ctx, const z2_lattice *lat, const z2_gramp_params *gp, void *state, int32_t k0,
+                            int32_t k1, void *stream, uint64_t *n_gates) {
+    if (!ctx || !lat) return fail(ctx, Z2_ERR_ARG, "NULL argument");
+    if (int rc = check_gramp(ctx, gp)) return rc;
+    if (int rc = check_state(ctx, state)) return rc;
+    if (k0 < 0 || k1 > gp->N_s || k0 > k1) return fail(ctx, Z2_ERR_ARG, "need 0 <= k0 <= k1 <= N_s");
+    const Lattice &L = lat->lat;
+    if (L.n_links + 1 > Z2_MAX_LINKS) return fail(ctx, Z2_ERR_LATTICE, "no room for the ancilla");
+    const bool c128 = gp->precision == Z2_C128, sym = gp->decomp == Z2_SYMMETRIC;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double tau = gp->t_s / gp->n;
+    uint64_t gates = 0;
+    for (int64_t j = (int64_t)k0 * gp->n + 1; j <= (int64_t)k1 * gp->n; ++j) {
+        const double g = (double)j * gp->g_s / gp->n;
+        if (sym)
+            if (int rc = enqueue_plaquettes_circuit(ctx, L, c128, state, tau / 2, st, gates)) return rc;
+        // exp(-i g X tau) = prod_l exp(i g tau sigma^x_l) = prod_l R_x(-2 g tau)
+        for (int l = 0; l < L.n_links; ++l)
+            if (int rc = enqueue_gate(ctx, L.n_links + 1, c128, state, Z2_GATE_RX, l, -1, -2.0 * g * tau, st)) return rc;
+        gates += L.n_links;
+        if (int rc = enqueue_plaquettes_circuit(ctx, L, c128, state, sym ? tau / 2 : tau, st, gates)) return rc;
+    }
+    if (n_gates) *n_gates = gates;
+    return Z2_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched runs.  A slot is a stream with its own state buffer and reduction
 // scratch; runs on one slot execute in stream order, slots run concurrently.
 struct RunSlot {
@@ -1369,10 +1650,12 @@ static void free_slots(std::vector<RunSlot> &slots) {
     slots.clear();
 }
 
-// |+>, the M steps and the observable reductions of one run, enqueued on st
+// |+>, the M steps and the observable reductions of one run, enqueued on st;
+// `after_init` (optional) is recorded once the |+> kernel has run
 static int enqueue_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params &p, void *state, cudaStream_t st,
-                       const Scratch &sc) {
+                       const Scratch &sc, cudaEvent_t after_init = nullptr) {
     if (int rc = z2_init_plus(ctx, lat, p.precision, state, st)) return rc;
+    if (after_init) Z2_CUDA(ctx, cudaEventRecord(after_init, st));
     if (int rc = z2_evolve(ctx, lat, &p, state, 0, p.M, st)) return rc;
     int n_out = 0;
     return measure_enqueue(ctx, lat, p.precision, state, nullptr, st, sc, &n_out);
@@ -1491,7 +1774,7 @@ static int sweep_persistent(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, in
             ++k;
         }
     }
-    const size_t partial_doubles = (size_t)reduce_blocks(max_n) * 32;
+    const size_t partial_doubles = reduce_partials_doubles(max_n);
     size_t max_bytes = 0;
     for (int i = 0; i < n; ++i)
         if (!persist[i])
@@ -1529,7 +1812,8 @@ static int sweep_persistent(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, in
     ck(cudaMemsetAsync(d_ctl, 0, persist_ctl_bytes(), st0), "clear control block");
     // 1) every persistent run evolved in one launch
     if (!runs.empty() && rc_all == Z2_OK) {
-        ck(launch_persistent(d_runs, (int)runs.size(), d_ctl, ctx->d_err, grid, st0), "persistent launch");
+        ck(launch_persistent(d_runs, (int)runs.size(), d_ctl, ctx->d_err, grid, st0, ctx->gang_wait_polls),
+           "persistent launch");
         ctx->launches += 1;
         // odd numbers of quarter turns: the final all-qubit flip of those runs
         for (size_t k = 0; k < runs.size() && rc_all == Z2_OK; ++k)
@@ -1622,7 +1906,7 @@ int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int
         free_slots(slots);
         if (h_all) cudaFreeHost(h_all);
     };
-    const size_t partial_doubles = (size_t)reduce_blocks(max_n) * 32;
+    const size_t partial_doubles = reduce_partials_doubles(max_n);
     for (auto &sl : slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaMalloc(&sl.state, max_bytes) != cudaSuccess ||
@@ -1705,12 +1989,14 @@ struct ServeReq {
     size_t bytes = 0;
     z2_results res{};
     Clock::time_point t_submit, t_start, t_end;
+    double dev_first = -1, dev_end = -1;  // device clock, seconds since the server's epoch event
 };
 
 struct ServeSlot {
     cudaStream_t st = nullptr;
     double *d_partials = nullptr, *d_out = nullptr, *h_out = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;        // end of the run's work (timing event)
+    cudaEvent_t ev_first = nullptr;  // after the run's first kernel (timing event)
     bool busy = false;
     uint64_t id = 0;
     void *state = nullptr;
@@ -1732,6 +2018,7 @@ struct z2_server {
     uint64_t next_id = 1;
     z2_serve_stats stats{};
     std::vector<ServeSlot> slots;
+    cudaEvent_t epoch = nullptr;  // device-clock origin of the request timestamps
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;  // worker-owned
     std::string last_error;
 };
@@ -1761,6 +2048,12 @@ void serve_worker(z2_server *srv) {
             const cudaError_t e = cudaEventQuery(sl.ev);
             if (e == cudaSuccess) {
                 measure_finish(sl.lat->lat, rq.spec.params.lambda, 1.0, sl.h_out, false, &rq.res);
+                float ms0 = 0, ms1 = 0;
+                if (cudaEventElapsedTime(&ms0, srv->epoch, sl.ev_first) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms1, srv->epoch, sl.ev) == cudaSuccess) {
+                    rq.dev_first = 1e-3 * ms0;
+                    rq.dev_end = 1e-3 * ms1;
+                }
             } else {
                 rq.res.status = Z2_ERR_CUDA;
             }
@@ -1812,7 +2105,7 @@ void serve_worker(z2_server *srv) {
                 rc = Z2_ERR_OOM;
             } else {
                 const Scratch sc{sl.d_partials, sl.d_out, sl.h_out};
-                rc = enqueue_run(ctx, lat, spec.params, state, sl.st, sc);
+                rc = enqueue_run(ctx, lat, spec.params, state, sl.st, sc, sl.ev_first);
                 if (rc == Z2_OK && cudaEventRecord(sl.ev, sl.st) != cudaSuccess) rc = Z2_ERR_CUDA;
             }
             lk.lock();
@@ -1868,22 +2161,36 @@ int z2_server_create(z2_ctx *ctx, size_t hbm_budget, int32_t max_slots, z2_serve
     srv->budget = hbm_budget;
     srv->max_slots = max_slots;
     srv->slots.resize(max_slots);
-    const size_t partial_doubles = (size_t)reduce_blocks(Z2_MAX_LINKS) * 32;
+    const size_t partial_doubles = reduce_partials_doubles(Z2_MAX_LINKS);
     for (auto &sl : srv->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&sl.ev) != cudaSuccess || cudaEventCreate(&sl.ev_first) != cudaSuccess ||
             cudaMalloc(&sl.d_partials, partial_doubles * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&sl.d_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess ||
             cudaMallocHost(&sl.h_out, OUT_DOUBLES * sizeof(double)) != cudaSuccess) {
             for (auto &x : srv->slots) {
                 if (x.st) cudaStreamDestroy(x.st);
                 if (x.ev) cudaEventDestroy(x.ev);
+                if (x.ev_first) cudaEventDestroy(x.ev_first);
                 if (x.d_partials) cudaFree(x.d_partials);
                 if (x.d_out) cudaFree(x.d_out);
                 if (x.h_out) cudaFreeHost(x.h_out);
             }
             return fail(ctx, Z2_ERR_OOM, "server: slot allocation failed");
         }
+    }
+    if (cudaEventCreate(&srv->epoch) != cudaSuccess || cudaEventRecord(srv->epoch, srv->slots[0].st) != cudaSuccess ||
+        cudaEventSynchronize(srv->epoch) != cudaSuccess) {
+        for (auto &x : srv->slots) {
+            cudaStreamDestroy(x.st);
+            cudaEventDestroy(x.ev);
+            cudaEventDestroy(x.ev_first);
+            cudaFree(x.d_partials);
+            cudaFree(x.d_out);
+            cudaFreeHost(x.h_out);
+        }
+        if (srv->epoch) cudaEventDestroy(srv->epoch);
+        return fail(ctx, Z2_ERR_CUDA, "server: epoch event failed");
     }
     z2_server *p = srv.release();
     p->worker = std::thread(serve_worker, p);
@@ -1970,6 +2277,18 @@ int z2_server_request_times(z2_server *srv, uint64_t ticket, double *queued_s, d
     return Z2_OK;
 }
 
+int z2_server_request_device_times(z2_server *srv, uint64_t ticket, double *first_s, double *end_s) {
+    if (!srv || !first_s || !end_s) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return Z2_ERR_NOT_FOUND;
+    const ServeReq &rq = it->second;
+    if (rq.phase != 2 || rq.dev_first < 0) return Z2_ERR_ARG;
+    *first_s = rq.dev_first;
+    *end_s = rq.dev_end;
+    return Z2_OK;
+}
+
 int z2_server_stats(z2_server *srv, z2_serve_stats *out) {
     if (!srv || !out) return Z2_ERR_ARG;
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -1998,10 +2317,12 @@ int z2_server_destroy(z2_server *srv) {
         if (x.st) cudaStreamSynchronize(x.st);
         if (x.st) cudaStreamDestroy(x.st);
         if (x.ev) cudaEventDestroy(x.ev);
+        if (x.ev_first) cudaEventDestroy(x.ev_first);
         if (x.d_partials) cudaFree(x.d_partials);
         if (x.d_out) cudaFree(x.d_out);
         if (x.h_out) cudaFreeHost(x.h_out);
     }
+    if (srv->epoch) cudaEventDestroy(srv->epoch);
     delete srv;
     return Z2_OK;
 }

@@ -66,3 +66,13 @@ def test_traffic_record_checks_kernel_and_source(tmp_path, monkeypatch):
     assert bench.recorded_traffic(32, "K<2>") is None       # another kernel
     src.write_bytes(b"// kernel source, edited\n")
     assert bench.recorded_traffic(32, "K<1>") is None       # the source changed since the capture
+
+
+def test_cpu_baseline_times_the_oracle_on_a_real_state():
+    # a workload of at most 30 links is timed on its own lattice (no scaling);
+    # at least one Trotter step even with a zero budget
+    wl = dict(d=2, L=(3, 2), lam=2.0, T=1.0, M=10)
+    cb = bench.cpu_baseline(wl, 1, budget_s=0.0)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
+    assert "3x2 lattice (12 qubits" in cb["sample"] and "extrapolated" not in cb["sample"]
+    assert cb["cpu"]

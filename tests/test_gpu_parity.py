@@ -101,8 +101,10 @@ def test_hadamard_layer(ctx, n, precision):
 
 
 @pytest.mark.parametrize("precision", PRECS)
-@pytest.mark.parametrize("n", [8, 18, 24])
+@pytest.mark.parametrize("n", [8, 12, 13, 14, 18, 24])
 def test_zsums_and_overlap(ctx, n, precision):
+    # n < 13: run-based kernel; n >= 13: chunked Walsh-Hadamard kernel (one
+    # block at 13 qubits); 42 + n masks = two launches of up to 64 masks
     psi = workloads.random_state(n, seed=9)
     phi = workloads.random_state(n, seed=10)
     rng = np.random.default_rng(n)
@@ -227,12 +229,23 @@ def test_3d_2x2x2_short_schedule_elementwise(ctx):
 
 
 @pytest.mark.parametrize("lam", [0.5, 1.0, 2.0, 3.0, 4.0, 6.0])
-def test_3d_lambda_sweep_invariants(ctx, lam):
-    # 2x2x2, T = 15, M = 300 symmetric: gauge invariance, sector and symmetry
+def test_3d_config_against_oracle(ctx, lam):
+    # the 3+1D configuration as stated: 2x2x2 periodic (24 links, 24
+    # plaquettes, Sec. 2.1), T = 15, M = 300 symmetric steps (Eq. s), complex64,
+    # every observable against the direct FP64 oracle; plus the exact
+    # invariants (Gauss law, the V sector, <W> = <sigma^z> = 0, cubic symmetry)
     lat = z2.Lattice(3, (2, 2, 2))
+    ol = OLattice(3, (2, 2, 2))
+    T, M = 15.0, 300
     g = torch.empty(1 << 24, dtype=torch.complex64, device="cuda")
-    res = z2.z2_run(ctx, lat.handle, z2.params(lam, 15.0, 300, 1, z2.Z2_C64), g)
-    d = z2.results_dict(res, lat.info)
+    res = z2.z2_run(ctx, lat.handle, z2.params(lam, T, M, 1, z2.Z2_C64), g)
+    psi = oracle.run(ol, lam, T, M, 1)
+    ref = oracle.observables(ol, psi, lam)
+    d = compare_obs(res, ref, lat, lam, z2.Z2_C64)
+    # the state itself: fidelity loss against the oracle's state <= 1e-6
+    got = host(g)
+    f = abs(np.vdot(psi, got)) ** 2 / (np.vdot(psi, psi).real * np.vdot(got, got).real)
+    assert 1 - f < 1e-6, 1 - f
     assert abs(d["norm"] - 1) < 1e-5
     assert np.max(np.abs(d["star"] - 1)) < 1e-5
     assert np.max(np.abs(d["vmu"] - 1)) < 1e-5

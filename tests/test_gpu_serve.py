@@ -1,6 +1,7 @@
 """Serving loop: requests that arrive while others run are admitted by HBM
 budget and overlap on the GPU (continuous batching); each result is the same
-alone and in the mix; budget rejection and cancellation work."""
+alone and in the mix, and matches the FP64 oracle (runs of up to 18 qubits);
+budget rejection and cancellation work."""
 
 import time
 
@@ -9,7 +10,9 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 import paper_1910_08020_gb300 as z2
+from oracle.lattice import Lattice as OLattice
 from paper_1910_08020_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +67,47 @@ def test_serve_mix_equals_alone(ctx):
         st = z2.z2_server_stats(srv)
         assert st.submitted == st.completed == len(reqs)
         assert st.hbm_peak <= 512 << 20 and st.hbm_in_use == 0 and st.active == 0
+        # each served result against the FP64 oracle (lattices of <= 18 links),
+        # at the run tolerances: 1e-5 (bounded observables), 1e-5 (N + lambda N_p)
+        # for the energy
+        checked = 0
+        for tk, rq in zip(tickets, reqs):
+            ol = OLattice(rq["d"], rq["L"])
+            if ol.n_links > 18:
+                continue
+            _, res = z2.z2_server_wait(srv, tk, timeout_s=10)
+            d = z2.results_dict(res, z2.Lattice(rq["d"], rq["L"]).info)
+            ref = oracle.observables(ol, oracle.run(ol, rq["lam"], rq["T"], rq["M"], 1), rq["lam"])
+            S = ol.n_links + abs(rq["lam"]) * ol.n_plaq
+            assert abs(d["energy"] - ref["energy"]) < 1e-5 * S
+            assert abs(d["norm"] - ref["norm"]) < 1e-5
+            assert np.max(np.abs(d["plaq"] - ref["plaq"])) < 1e-5
+            assert np.max(np.abs(d["sigmax"] - ref["sigmax"])) < 1e-5
+            assert np.max(np.abs(d["star"] - ref["star"])) < 1e-5
+            checked += 1
+        assert checked >= 10
+    finally:
+        z2.z2_server_destroy(srv)
+
+
+def test_served_runs_overlap_on_device(ctx):
+    # Two 24-qubit runs submitted together to a two-slot server: the second
+    # run's first kernel completes while the first run is still on the GPU
+    # (device-clock events on the runs' streams), which a server that ran one
+    # request at a time could not show.
+    srv = z2.z2_server_create(ctx, hbm_budget=1 << 30, max_slots=2)
+    try:
+        spec = dict(d=2, L=(4, 3), lam=2.0, T=8.0, M=200)
+        tks = [z2.z2_server_submit(srv, spec) for _ in range(2)]
+        iv = []
+        for tk in tks:
+            rc, res = z2.z2_server_wait(srv, tk, timeout_s=120)
+            assert rc == 0 and abs(res.norm - 1) < 1e-5
+            iv.append(z2.z2_server_request_device_times(srv, tk))
+        (a0, a1), (b0, b1) = iv
+        assert a0 < a1 and b0 < b1
+        both = min(a1, b1) - max(a0, b0)
+        assert both > 0.25 * min(a1 - a0, b1 - b0), iv
     finally:
         z2.z2_server_destroy(srv)
 

@@ -126,3 +126,26 @@ def test_persistent_sweep_paper_mix(ctx):
             ol = OLattice(sp["d"], sp["L"])
             ref = oracle.observables(ol, oracle.run(ol, sp["lam"], sp["T"], sp["M"], 1), sp["lam"])
             assert abs(r.energy - ref["energy"]) < 1e-5 * (ol.n_links + sp["lam"] * ol.n_plaq)
+
+
+def test_persistent_gang_wait_runs_out_then_recovers(ctx):
+    # Failure detection without a GPU fault.  The persistent kernel's gang
+    # barrier is a bounded poll of a counter in global memory, with no copies
+    # in flight.  With the limit at one poll, a CTA that reaches a barrier
+    # before the rest of its gang gives up at once, sets the device error
+    # flag and returns; the gang's other CTAs give up at their next barrier,
+    # and the call reports Z2_ERR_DEVICE_TIMEOUT with a message.  Over the
+    # many barriers of a sweep some CTA is always early.  The context then
+    # runs the same sweep normally.
+    specs = small_specs(8, seed=12)
+    assert any(z2.Lattice(sp["d"], sp["L"]).n_links >= 14 for sp in specs)
+    z2.z2_ctx_set_option(ctx, z2.Z2_OPT_GANG_WAIT_POLLS, 1)
+    try:
+        with pytest.raises(z2.Z2Error) as e:
+            z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_PERSISTENT, n_streams=2)
+        assert e.value.code == -6
+        assert "gave up" in str(e.value)
+    finally:
+        z2.z2_ctx_set_option(ctx, z2.Z2_OPT_GANG_WAIT_POLLS, 0)
+    res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_PERSISTENT, n_streams=2)
+    assert all(r.status == 0 and abs(r.norm - 1) < 1e-5 for r in res)
