@@ -124,6 +124,8 @@ def kernel_name(variant, info):
         if info.low_tile_bits != info.tile_bits:  # low group on the smaller tile
             return f"pass_kernel_ring<{info.low_tile_bits},4,RX>+<{info.tile_bits},4,RX>"
         return f"pass_kernel_ring<{info.tile_bits},4,RX>"
+    if variant == 0 and info.n_groups == 2 and info.tile_bits == 14 and info.low_tile_bits == 13:
+        return "pass_kernel_ring<13,4,RX>+pass_kernel_packed<14,4,RX>"
     if variant == 2:
         return f"pass_kernel_tma<float2,{info.tile_bits},RX>"
     return f"pass_kernel_packed<{info.tile_bits},4,RX>"
@@ -465,9 +467,14 @@ def main():
     elapsed, value = aggregate(elapsed, wl["M"] * args.steps, dist, device="cuda")
     pass_launches = info.n_passes * args.steps
     avg_pass = evolve_s / pass_launches
-    alg_bytes = 2.0 * state_bytes  # read + write of the state per pass
+    # algorithmic unit: one Trotter step reads and writes the state once
+    # (16 * 2^N bytes); one pass launch advances M / n_passes of a step
+    step_bytes = 2.0 * state_bytes
+    steps_per_launch = wl["M"] / info.n_passes
+    alg_bytes = step_bytes * steps_per_launch
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_pass / 1e9
+    pass_gbs = step_bytes / avg_pass / 1e9  # streaming rate of a pass (reads + writes the state once)
 
     # end to end through the public API: plans (phase tables, pass lists) are
     # rebuilt and uploaded from host memory every step, results read back
@@ -506,7 +513,10 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind,
                          "traffic": recorded_traffic(n, kname),
-                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3},
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_pass * 1e3,
+                         "unit_of_work": "one Trotter step = one read + one write of the state "
+                                         f"({step_bytes / 1e9:.3f} GB); {steps_per_launch:.4f} steps per launch",
+                         "per_pass": {"bytes": step_bytes, "achieved": pass_gbs, "frac": pass_gbs / peak}},
             "e2e": {"value": e2e_v, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": ck,
             "result": {"energy": d["energy"], "mean_plaq": d["mean_plaq"], "wilson_2x2": d["wilson_2x2"],

@@ -96,11 +96,16 @@ int tma_tile_limit(bool c128);
 // step per launch, tile bits 10..13, grid = number of SMs
 // s8: relayouts through 8-byte (re | im) slot arrays instead of 16-byte pair
 // slots (used for strided passes, see pass_packed.cuh)
+// seq: static layout sequence code of the pass (ring_seq in runtime.cpp; 0 =
+// the general step); launchers fall back to the general step where no static
+// instantiation exists
 cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8);
+                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8,
+                                 int seq = 0);
 // the same ring with 32 pairs per thread (pass_c64_ring5.cu), tile bits 12..13
 cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8);
+                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8,
+                                  int seq = 0);
 int tma_smem_bytes(bool c128, int tb);
 size_t pass_smem(bool c128, int tb);
 cudaError_t launch_init_plus(bool c128, void *state, int n, int grid, cudaStream_t st);

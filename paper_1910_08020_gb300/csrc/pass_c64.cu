@@ -51,7 +51,7 @@ cudaError_t launch_pass_c64(int tb, int op, void *psi, const PassArgs &a, const 
 
 int packed_threads(int tb) { return 1 << (tb - 1 - PACK_W); }
 
-template <int TB, int OP, bool S8 = false>
+template <int TB, int OP, bool S8 = false, int SEQ = 0>
 static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps,
                                   const float2 *tables, int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, PACK_W>;
@@ -59,13 +59,13 @@ static cudaError_t launch_ring_tb(const PassArgs &a, const CUtensorMap &m, const
     static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
     const uint64_t dev_bit = current_device_bit();
     if (!(configured.load() & dev_bit)) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP, S8>,
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, PACK_W, OP, S8, SEQ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured |= dev_bit;
     }
-    pass_kernel_ring<TB, PACK_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
-                                                                                      err);
+    pass_kernel_ring<TB, PACK_W, OP, S8, SEQ><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables,
+                                                                                           fmt, err);
     return cudaGetLastError();
 }
 
@@ -82,10 +82,17 @@ static cudaError_t launch_ring_op(int tb, const PassArgs &a, const CUtensorMap &
 }
 
 cudaError_t launch_pass_ring_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8) {
+                                 const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8, int seq) {
     auto ps = static_cast<const PassStep *>(steps);
     auto tab = static_cast<const float2 *>(tables);
     const CUtensorMap &m = *static_cast<const CUtensorMap *>(tmap);
+    // static layout sequences of the large-state plans: the unmerged low-group
+    // pass on 12-bit tiles (32 qubits) and the merged low-group pass on 13-bit
+    // tiles (24 qubits); any other pass runs the general step
+    if (!s8 && op == OP_RX_TAN && tb == 12 && seq == seq_code(3, false))
+        return launch_ring_tb<12, OP_RX_TAN, false, seq_code(3, false)>(a, m, ps, tab, fmt, err, grid, st);
+    if (!s8 && op == OP_RX_TAN && tb == 13 && seq == seq_code(3, true))
+        return launch_ring_tb<13, OP_RX_TAN, false, seq_code(3, true)>(a, m, ps, tab, fmt, err, grid, st);
     // 8-byte relayout scratch for the evolution's strided passes on 12- and
     // 13-bit tiles (instruction-bound); the rest keep 16-byte pair slots
     if (s8 && op == OP_RX_TAN && tb == 12)

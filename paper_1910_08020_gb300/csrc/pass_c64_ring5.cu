@@ -12,7 +12,7 @@ namespace z2 {
 namespace {
 constexpr int RING5_W = 5;
 
-template <int TB, int OP, bool S8 = false>
+template <int TB, int OP, bool S8 = false, int SEQ = 0>
 cudaError_t launch_ring5_tb(const PassArgs &a, const CUtensorMap &m, const PassStep *steps, const float2 *tables,
                             int fmt, int *err, int grid, cudaStream_t st) {
     using T = PTile<TB, RING5_W>;
@@ -20,13 +20,13 @@ cudaError_t launch_ring5_tb(const PassArgs &a, const CUtensorMap &m, const PassS
     static std::atomic<uint64_t> configured{0};  // devices whose attributes are set
     const uint64_t dev_bit = current_device_bit();
     if (!(configured.load() & dev_bit)) {
-        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, RING5_W, OP, S8>,
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel_ring<TB, RING5_W, OP, S8, SEQ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured |= dev_bit;
     }
-    pass_kernel_ring<TB, RING5_W, OP, S8><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables, fmt,
-                                                                                        err);
+    pass_kernel_ring<TB, RING5_W, OP, S8, SEQ><<<grid, RT::NW * T::NT, RT::SMEM_BYTES, st>>>(a, m, steps, tables,
+                                                                                             fmt, err);
     return cudaGetLastError();
 }
 
@@ -42,10 +42,16 @@ cudaError_t launch_ring5_op(int tb, const PassArgs &a, const CUtensorMap &m, con
 }  // namespace
 
 cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void *tmap, const void *steps,
-                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8) {
+                                  const void *tables, int fmt, int *err, int grid, cudaStream_t st, bool s8, int seq) {
     auto ps = static_cast<const PassStep *>(steps);
     auto tab = static_cast<const float2 *>(tables);
     const CUtensorMap &m = *static_cast<const CUtensorMap *>(tmap);
+    // the merged strided passes of the large-state plans: both rotations in
+    // register layouts 0 and 1 (static sequence); any other pass: general step
+    if (s8 && op == OP_RX_TAN && tb == 13 && seq == seq_code(2, true))
+        return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
+    if (s8 && op == OP_RX_TAN && tb == 12 && seq == seq_code(2, true))
+        return launch_ring5_tb<12, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 12)
         return launch_ring5_tb<12, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 13)

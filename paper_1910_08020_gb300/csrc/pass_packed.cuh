@@ -329,6 +329,54 @@ __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], cons
     }
 }
 
+// Static layout sequences.  pstep chooses at run time which register
+// layouts a pass visits; the join points of those choices cost register
+// moves.  When the host knows that rot1 and rot2 lie in the register bits of
+// layouts 0 .. L-1, pstep_static visits exactly those in a fixed order: rot1
+// up through layouts 0 .. L-1, the mid step in layout L-1, then rot2 back down
+// to layout 0 (R2), or, for a pass without a second rotation, one relayout
+// back to layout 0.  Every rotated bit is rotated once in its own layout, as
+// in pstep, so the result is the same.
+template <int TB, int W, int OP, bool S8, int Q, int L>
+__device__ __forceinline__ void seq_up(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, float g1,
+                                       ulonglong2 *sm, uint32_t t, int bar) {
+    if constexpr (Q < L) {
+        prelayout<TB, W, Q - 1, Q, S8>(re, im, sm, t, bar);
+        prot<TB, W, Q, OP>(re, im, st.rot1 & ~1u, g1);
+        seq_up<TB, W, OP, S8, Q + 1, L>(re, im, st, g1, sm, t, bar);
+    }
+}
+
+// in layout Q + 1: move to layout Q and apply its rot2 bits, down to layout 0
+template <int TB, int W, int OP, bool S8, int Q>
+__device__ __forceinline__ void seq_down(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, float g2,
+                                         ulonglong2 *sm, uint32_t t, int bar) {
+    if constexpr (Q >= 0) {
+        prelayout<TB, W, Q + 1, Q, S8>(re, im, sm, t, bar);
+        prot<TB, W, Q, OP>(re, im, Q == 0 ? st.rot2 : (st.rot2 & ~1u), g2);
+        seq_down<TB, W, OP, S8, Q - 1>(re, im, st, g2, sm, t, bar);
+    }
+}
+
+template <int TB, int W, int OP, bool S8, int L, bool R2>
+__device__ __forceinline__ void pstep_static(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st,
+                                             const PassArgs &a, float g1, float g2, uint32_t ptile, uint32_t t,
+                                             ulonglong2 *sm, const float *tabr, const float *tabi, int bar) {
+    static_assert(L >= 1 && L <= PTile<TB, W>::K, "static sequence beyond the tile's layouts");
+    prot<TB, W, 0, OP>(re, im, st.rot1, g1);
+    seq_up<TB, W, OP, S8, 1, L>(re, im, st, g1, sm, t, bar);
+    pmid<TB, W, L - 1>(re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
+    if constexpr (R2) {
+        prot<TB, W, L - 1, OP>(re, im, L - 1 == 0 ? st.rot2 : (st.rot2 & ~1u), g2);
+        seq_down<TB, W, OP, S8, L - 2>(re, im, st, g2, sm, t, bar);
+    } else if constexpr (L > 1) {
+        prelayout<TB, W, L - 1, 0, S8>(re, im, sm, t, bar);
+    }
+}
+
+// SEQ template argument of the ring kernel: 0 = pstep, else 2 L + R2
+constexpr int seq_code(int L, bool R2) { return 2 * L + (R2 ? 1 : 0); }
+
 // Ask the TMA unit to pull a tile into L2 ahead of its use (no completion is
 // tracked: a prefetch never blocks and never faults on in-range addresses).
 // The tile is 2^(TB-c) rows of 2^c contiguous complex64 amplitudes, row r at
@@ -465,7 +513,7 @@ __device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
     return r != 0;
 }
 
-template <int TB, int W, int OP, bool S8 = false>
+template <int TB, int W, int OP, bool S8 = false, int SEQ = 0>
 __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     pass_kernel_ring(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
                      const PassStep *__restrict__ steps, const float2 *__restrict__ tables, int fmt, int *err) {
@@ -576,7 +624,11 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
             }
         }
         tile_sync<T::NT>(bar);  // dense reads done before the padded layouts reuse the buffer
-        pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, bar);
+        if constexpr (SEQ == 0)
+            pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, bar);
+        else
+            pstep_static<TB, W, OP, S8, SEQ / 2, (SEQ & 1) != 0>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t,
+                                                                 sm, tabr, tabi, bar);
         tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
         if (out_split) {
 #pragma unroll

@@ -90,6 +90,7 @@ struct Plan {
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
     bool ring_wide = false;            // ... with 32 pairs per thread
     bool strided_wide = false;         // ... for the strided groups only (variant 5)
+    bool ring_low = false;             // only the low group on the ring, the others on the direct kernel
     int variant = 0;                   // the kernel variant the plan was built for
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
@@ -240,6 +241,17 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
             n_low = tb_low;
             rem = rem1;
         }
+    }
+    // Automatic plans on the 14-bit direct kernel with a single strided group
+    // (24 qubits): the low group moves to a 13-bit tile on the TMA ring when
+    // the strided group can take the extra bit with at least CMIN passenger
+    // bits.  Both passes stay merged, one per Trotter step; the ring streams
+    // the low group's merged passes where the direct kernel holds one tile per
+    // SM with nothing to overlap its loads.
+    if (!c128 && variant == 0 && !tb_override && tma && tb == 14 && h == 1 && n_low == tb && n - 13 <= kmax(tb)) {
+        tb_low = 13;
+        n_low = 13;
+        rem = n - 13;
     }
     g.tb = tb;
     Group low;
@@ -539,7 +551,33 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     // automatic: the strided groups on 32 pairs per thread where that kernel
     // exists (measured fastest at 32 qubits: variant 5 over 3 and 4)
     P.strided_wide = P.ring && (P.variant == 5 || (P.variant == 0 && P.geo.tb >= 12));
+    // a low group on a ring-sized tile beside direct-kernel strided groups
+    // (plan_geometry's 24-qubit rule)
+    P.ring_low = !c128 && !P.ring && !P.tma && P.geo.groups.size() > 1 && P.geo.groups[0].tb <= 13 &&
+                 P.geo.groups[0].tb >= 10 && P.geo.groups[0].tb < P.geo.tb && encode_fn() != nullptr;
     return Z2_OK;
+}
+
+// Pair-index bits owned by register layout q of a complex64 tile of tb bits
+// with 2^W pairs per thread (the host copy of PTile::ownY in pass_packed.cuh).
+uint32_t layout_own_bits(int tb, int W, int q) {
+    const int Y = tb - 1, K = (Y + W - 1) / W;
+    if (q == K - 1) return (1u << (Y - q * W)) - 1u;
+    const int w0 = std::max(Y - W * (q + 1), 0);
+    return ((1u << W) - 1u) << w0;
+}
+
+// Static layout sequence of a ring pass (pstep_static): the fewest layouts
+// 0 .. L-1 that hold every rotated bit of rot1 and rot2, coded 2 L + (rot2 != 0).
+int ring_seq(int tb, int W, const PassStepHost &s) {
+    const int Y = tb - 1, K = (Y + W - 1) / W;
+    const uint32_t bits = (s.rot1 | s.rot2) >> 1;
+    uint32_t cover = 0;
+    for (int L = 1; L <= K; ++L) {
+        cover |= layout_own_bits(tb, W, L - 1);
+        if (!(bits & ~cover)) return 2 * L + (s.rot2 ? 1 : 0);
+    }
+    return 0;
 }
 
 // effective tile size and kernel variant for a state of n qubits: explicit
@@ -707,12 +745,14 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
                 const int grid = (int)std::min<uint64_t>((nt + 1) / 2, (uint64_t)ctx->sm_count);
                 const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
                 const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
-                if (P.ring_wide || (P.strided_wide && gi != 0))
+                const bool wide = P.ring_wide || (P.strided_wide && gi != 0);
+                const int seq = ring_seq(tb, wide ? 5 : 4, P.passes[i].step);
+                if (wide)
                     Z2_CUDA(ctx, launch_pass_ring5_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
-                                                       ctx->d_err, grid, st, P.strided_wide));
+                                                       ctx->d_err, grid, st, P.strided_wide, seq));
                 else
                     Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[gi], &tmaps[gi], sp, P.d_tables, fmt,
-                                                      ctx->d_err, grid, st, gi != 0));
+                                                      ctx->d_err, grid, st, gi != 0, seq));
             }
             ctx->launches += P.passes.size();
             if (P.flip) {
@@ -737,6 +777,32 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
             }
             ctx->launches += P.passes.size();
         }
+    } else if (P.ring_low && !P.passes.empty()) {
+        // low-group passes on the ring (TMA view of the low group), the others
+        // on the direct kernel; the split-pair format flows between both
+        CUtensorMap tmap0;
+        int lo_bits = 0, hi_dim = 4;
+        if (!make_tensor_map(&tmap0, state, g.n, g.groups[0].tb, g.groups[0], false, lo_bits, hi_dim))
+            return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        P.args[0].tma_lo_bits = lo_bits;
+        P.args[0].tma_hi_dim = hi_dim;
+        const size_t last = P.passes.size() - 1;
+        for (size_t i = 0; i < P.passes.size(); ++i) {
+            const int gi = P.passes[i].group;
+            const int tb = g.groups[gi].tb;
+            const uint64_t nt = 1ull << (g.n - tb);
+            const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
+            const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
+            if (gi == 0) {
+                const int grid = (int)std::min<uint64_t>((nt + 1) / 2, (uint64_t)ctx->sm_count);
+                Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[0], &tmap0, sp, P.d_tables, fmt, ctx->d_err, grid,
+                                                  st, false, ring_seq(tb, 4, P.passes[i].step)));
+            } else {
+                const int grid = (int)std::min<uint64_t>(nt, 1u << 20);
+                Z2_CUDA(ctx, launch_pass_steps(false, tb, P.op, state, P.args[gi], sp, 1, P.d_tables, fmt, grid, st));
+            }
+        }
+        ctx->launches += P.passes.size();
     } else if (!P.passes.empty()) {
         const int grid = (int)std::min<uint64_t>(ntiles, 1u << 20);
         if (single) {

@@ -122,6 +122,20 @@ def test_no_extra_pass_for_the_smaller_low_tile():
             assert len(check_plan(n, tb, 3, True)) == len(check_plan(n, tb, 3, False))
 
 
+def test_24_qubit_mixed_plan():
+    # 24 qubits: the low group on a 13-bit ring tile, the 11 strided bits on a
+    # 14-bit direct-kernel tile with 3 passenger bits (64-byte rows); one merged
+    # pass per Trotter step either way.  Forced 14-bit tiles, another variant or
+    # no tensor-map encoder keep the 14 + 10 plan.
+    g = check_plan(24, 0, 0, True)
+    assert [(x.tile_bits, x.c, x.b, x.k) for x in g] == [(13, 13, 13, 13), (14, 3, 13, 11)]
+    for tb, variant, tma in ((14, 0, True), (0, 1, True), (0, 0, False)):
+        g = check_plan(24, tb, variant, tma)
+        assert [(x.tile_bits, x.k) for x in g] == [(14, 14), (14, 10)]
+    for n in (22, 23, 25):  # other sizes keep their plans
+        assert check_plan(n, 0, 0, True)[0].tile_bits != 13 or n == 23
+
+
 def test_rejects_bad_arguments():
     for args in ((7, 0, 0, 0, True), (35, 0, 0, 0, True), (20, 5, 0, 0, True), (20, 0, 15, 0, True),
                  (20, 0, 0, 6, True)):
