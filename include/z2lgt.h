@@ -423,9 +423,10 @@ typedef struct {
 #define Z2_SWEEP_PLAIN 0   /* one run after another on one stream, each synchronised            */
 #define Z2_SWEEP_STREAMS 1 /* runs spread over n_streams streams, all enqueued before one wait  */
 #define Z2_SWEEP_GRAPHS 2  /* as STREAMS, each run (|+>, M steps, observables) one CUDA graph   */
-#define Z2_SWEEP_PERSISTENT 3 /* every complex64 run of >= 14 qubits evolved in one persistent
+#define Z2_SWEEP_PERSISTENT 3 /* every complex64 run of 14 to 21 qubits evolved in one persistent
                                  launch (gangs of co-resident CTAs take runs from a device queue);
-                                 observables and the other runs follow on n_streams streams    */
+                                 observables and the other runs follow on n_streams streams
+                                 (runs of 22 or more qubits fill the GPU with their own plans) */
 
 /* Runs specs[0 .. n) (each: |+>^N, M steps, observables at s = 1, no
  * fidelity) and writes out[i]; out[i].status is that run's status.  The
@@ -438,8 +439,9 @@ int z2_sweep(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t mode, int
 
 /* ---- serving: a request loop with continuous batching --------------------
  * A server owns a worker thread that admits submitted runs in arrival order
- * as soon as a run slot is free and the run's device memory (its state plus
- * reduction scratch) fits the HBM budget, starts each on its own stream (so
+ * (within the size classes of z2_server_set_option) as soon as a run slot is
+ * free and the run's device memory (its state) fits the HBM budget, starts
+ * each on its own stream (so
  * runs that arrive while others are on the GPU overlap with them), keeps its
  * state resident until it finishes, then returns the memory.  A run's result
  * does not depend on what else is running.  While a server exists its
@@ -455,6 +457,17 @@ typedef struct {
 /* hbm_budget: device bytes the server may hold for run states (0 = 80% of
  * the free memory); max_slots: most runs on the GPU at once (1..64). */
 int z2_server_create(z2_ctx *ctx, size_t hbm_budget, int32_t max_slots, z2_server **out);
+/* Admission by size class.  A run of at least Z2_SERVE_OPT_LARGE_QUBITS
+ * qubits (default 22) fills every SM with each of its pass kernels, so
+ * running several such runs at once only interleaves them; at most
+ * Z2_SERVE_OPT_MAX_LARGE of them (default 2) are admitted at a time.  Smaller
+ * runs take any free slot beside them, passing a large run that waits only for
+ * a large-run place (it keeps its place in the queue).  The HBM budget still
+ * admits in arrival order.  Z2_ERR_ARG for values out of range (large_qubits
+ * 1..35, max_large 1..64) or for changing the class size while runs are active. */
+#define Z2_SERVE_OPT_LARGE_QUBITS 0
+#define Z2_SERVE_OPT_MAX_LARGE 1
+int z2_server_set_option(z2_server *srv, int32_t option, int32_t value);
 /* Queue a run; *ticket identifies it.  Z2_ERR_BUDGET if it can never fit. */
 int z2_server_submit(z2_server *srv, const z2_run_spec *spec, uint64_t *ticket);
 /* *done = 1 once the run has finished (then *out holds its results, with

@@ -30,7 +30,8 @@ __all__ = [
     "trajectory", "finite_differences",
     "Context", "Lattice", "results_dict", "z2_sweep", "RunSpec", "run_specs", "ServeStats",
     "z2_server_create", "z2_server_submit", "z2_server_poll", "z2_server_wait", "z2_server_cancel",
-    "z2_server_stats", "z2_server_request_times", "z2_server_request_device_times", "z2_server_destroy",
+    "z2_server_stats", "z2_server_request_times", "z2_server_request_device_times", "z2_server_set_option", "Z2_SERVE_OPT_LARGE_QUBITS",
+    "Z2_SERVE_OPT_MAX_LARGE", "z2_server_destroy",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -162,6 +163,7 @@ _SIGS = {
     "z2_server_stats": [_P, ctypes.POINTER(ServeStats)],
     "z2_server_request_times": [_P, ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "z2_server_request_device_times": [_P, ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "z2_server_set_option": [_P, _I, _I],
     "z2_server_destroy": [_P],
 }
 
@@ -530,6 +532,13 @@ def z2_server_request_device_times(srv, ticket):
     _scheck(load().z2_server_request_device_times(srv, ticket, ctypes.byref(a), ctypes.byref(b)),
             "request device times")
     return a.value, b.value
+
+
+Z2_SERVE_OPT_LARGE_QUBITS, Z2_SERVE_OPT_MAX_LARGE = 0, 1
+
+
+def z2_server_set_option(srv, option, value):
+    _scheck(load().z2_server_set_option(srv, int(option), int(value)), "server option")
 
 
 def z2_server_destroy(srv):

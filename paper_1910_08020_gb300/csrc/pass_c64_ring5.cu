@@ -52,6 +52,9 @@ cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void 
         return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 12 && seq == seq_code(2, true))
         return launch_ring5_tb<12, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
+    // the 24-qubit strided group (two passenger bits): its bits reach layout 2
+    if (s8 && op == OP_RX_TAN && tb == 13 && seq == seq_code(3, true))
+        return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(3, true)>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 12)
         return launch_ring5_tb<12, OP_RX_TAN, true>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 13)

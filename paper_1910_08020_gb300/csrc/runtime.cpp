@@ -90,7 +90,6 @@ struct Plan {
     bool ring = false;                 // complex64 TMA ring kernel (multi-tile passes)
     bool ring_wide = false;            // ... with 32 pairs per thread
     bool strided_wide = false;         // ... for the strided groups only (variant 5)
-    bool ring_low = false;             // only the low group on the ring, the others on the direct kernel
     int variant = 0;                   // the kernel variant the plan was built for
     ~Plan() {
         if (d_steps) cudaFree(d_steps);
@@ -243,15 +242,31 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         }
     }
     // Automatic plans on the 14-bit direct kernel with a single strided group
-    // (24 qubits): the low group moves to a 13-bit tile on the TMA ring when
-    // the strided group can take the extra bit with at least CMIN passenger
-    // bits.  Both passes stay merged, one per Trotter step; the ring streams
-    // the low group's merged passes where the direct kernel holds one tile per
-    // SM with nothing to overlap its loads.
-    if (!c128 && variant == 0 && !tb_override && tma && tb == 14 && h == 1 && n_low == tb && n - 13 <= kmax(tb)) {
-        tb_low = 13;
-        n_low = 13;
-        rem = n - 13;
+    // of at most 11 bits (24 qubits): both groups move to 13-bit tiles on the
+    // TMA ring, the low group with 13 bits and the strided group with only 2
+    // passenger bits (32-byte rows).  Both passes stay merged, one per Trotter
+    // step.  The direct kernel holds one 14-bit tile per SM and waits for each
+    // load; the ring streams.  At 24 qubits the state is about the size of L2
+    // (57% of the sectors hit), where short rows cost little: measured 10.98k
+    // Trotter steps/s against 10.23k with the strided group on 14-bit direct
+    // tiles (3 passenger bits) and 8.35k for 14 + 10 on the direct kernel.
+    if (!c128 && variant == 0 && !tb_override && tma && tb == 14 && h == 1 && n_low == tb && n - 13 <= 11 &&
+        n - 13 >= kmin(13)) {
+        g.tb = 13;
+        Group lo;
+        lo.lo = 0;
+        lo.hi = lo.k = lo.k1 = lo.tb = lo.c = lo.b = 13;
+        lo.rot = (1u << 13) - 1u;
+        Group st;
+        st.lo = st.b = 13;
+        st.hi = n;
+        st.k = st.k1 = n - 13;
+        st.tb = 13;
+        st.c = 13 - st.k;
+        st.rot = ((1u << st.k) - 1u) << st.c;
+        g.groups = {lo, st};
+        g.order = {0, 1};
+        return true;
     }
     g.tb = tb;
     Group low;
@@ -345,7 +360,8 @@ bool plan_geometry(int n, bool c128, int tb_override, int variant, Geometry &g, 
         }
     }
     // low group in the middle so that the merged boundary passes are the
-    // cheaper strided ones
+    // cheaper strided ones (measured at 32 qubits with the static layout
+    // sequences: 36.6 Trotter steps/s against 29.7 with the low group merged)
     if (g.groups.size() >= 3) {
         g.order.push_back(1);
         g.order.push_back(0);
@@ -551,10 +567,6 @@ int upload_plan(z2_ctx *ctx, const Lattice &lat, Plan &P) {
     // automatic: the strided groups on 32 pairs per thread where that kernel
     // exists (measured fastest at 32 qubits: variant 5 over 3 and 4)
     P.strided_wide = P.ring && (P.variant == 5 || (P.variant == 0 && P.geo.tb >= 12));
-    // a low group on a ring-sized tile beside direct-kernel strided groups
-    // (plan_geometry's 24-qubit rule)
-    P.ring_low = !c128 && !P.ring && !P.tma && P.geo.groups.size() > 1 && P.geo.groups[0].tb <= 13 &&
-                 P.geo.groups[0].tb >= 10 && P.geo.groups[0].tb < P.geo.tb && encode_fn() != nullptr;
     return Z2_OK;
 }
 
@@ -777,32 +789,6 @@ int exec_plan(z2_ctx *ctx, Plan &P, void *state, cudaStream_t st) {
             }
             ctx->launches += P.passes.size();
         }
-    } else if (P.ring_low && !P.passes.empty()) {
-        // low-group passes on the ring (TMA view of the low group), the others
-        // on the direct kernel; the split-pair format flows between both
-        CUtensorMap tmap0;
-        int lo_bits = 0, hi_dim = 4;
-        if (!make_tensor_map(&tmap0, state, g.n, g.groups[0].tb, g.groups[0], false, lo_bits, hi_dim))
-            return fail(ctx, Z2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-        P.args[0].tma_lo_bits = lo_bits;
-        P.args[0].tma_hi_dim = hi_dim;
-        const size_t last = P.passes.size() - 1;
-        for (size_t i = 0; i < P.passes.size(); ++i) {
-            const int gi = P.passes[i].group;
-            const int tb = g.groups[gi].tb;
-            const uint64_t nt = 1ull << (g.n - tb);
-            const void *sp = static_cast<const char *>(P.d_steps) + i * step_bytes;
-            const int fmt = (i > 0 ? 1 : 0) | (i < last ? 2 : 0);
-            if (gi == 0) {
-                const int grid = (int)std::min<uint64_t>((nt + 1) / 2, (uint64_t)ctx->sm_count);
-                Z2_CUDA(ctx, launch_pass_ring_c64(tb, P.op, P.args[0], &tmap0, sp, P.d_tables, fmt, ctx->d_err, grid,
-                                                  st, false, ring_seq(tb, 4, P.passes[i].step)));
-            } else {
-                const int grid = (int)std::min<uint64_t>(nt, 1u << 20);
-                Z2_CUDA(ctx, launch_pass_steps(false, tb, P.op, state, P.args[gi], sp, 1, P.d_tables, fmt, grid, st));
-            }
-        }
-        ctx->launches += P.passes.size();
     } else if (!P.passes.empty()) {
         const int grid = (int)std::min<uint64_t>(ntiles, 1u << 20);
         if (single) {
@@ -1727,6 +1713,10 @@ static int enqueue_run(z2_ctx *ctx, const z2_lattice *lat, const z2_run_params &
     return measure_enqueue(ctx, lat, p.precision, state, nullptr, st, sc, &n_out);
 }
 
+// runs of this many qubits or more fill every SM with one pass kernel of their
+// own plan (ring tiles), faster than the persistent kernel's fixed tiles
+constexpr int PERSIST_MAX_QUBITS = 22;
+
 static int sweep_persistent(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, int32_t n_streams, z2_results *out) {
     const int PT = persist_tile_bits();
     // lattices and, for the runs the persistent kernel takes, plans with its tile size
@@ -1757,7 +1747,11 @@ static int sweep_persistent(z2_ctx *ctx, const z2_run_spec *specs, int32_t n, in
         lat_of[i] = it->second.get();
         const int nl = lat_of[i]->lat.n_links;
         max_n = std::max(max_n, nl);
-        persist[i] = sp.params.precision == Z2_C64 && nl >= PT;
+        // the persistent kernel takes the runs whose passes do not fill the GPU
+        // (fewer than PERSIST_MAX_QUBITS qubits), where a launch per pass is
+        // the cost it removes; larger runs go through their own plans on the
+        // streams after it
+        persist[i] = sp.params.precision == Z2_C64 && nl >= PT && nl < PERSIST_MAX_QUBITS;
         if (persist[i]) {
             ctx->tb_override = PT;
             ctx->variant = 1;
@@ -2053,6 +2047,7 @@ struct ServeReq {
     z2_run_spec spec{};
     int phase = 0;  // 0 queued, 1 running, 2 finished, 3 cancelled
     size_t bytes = 0;
+    int qubits = 0;
     z2_results res{};
     Clock::time_point t_submit, t_start, t_end;
     double dev_first = -1, dev_end = -1;  // device clock, seconds since the server's epoch event
@@ -2084,6 +2079,13 @@ struct z2_server {
     uint64_t next_id = 1;
     z2_serve_stats stats{};
     std::vector<ServeSlot> slots;
+    // size classes: runs of at least large_qubits qubits fill every SM with one
+    // pass kernel, so running several at once only interleaves them; at most
+    // max_large of them are admitted at a time, while smaller runs take any
+    // free slot beside them (Z2_SERVE_OPT_*)
+    int large_qubits = 22;
+    int max_large = 2;
+    int active_large = 0;
     cudaEvent_t epoch = nullptr;  // device-clock origin of the request timestamps
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<z2_lattice>> lats;  // worker-owned
     std::string last_error;
@@ -2127,6 +2129,7 @@ void serve_worker(z2_server *srv) {
             srv->stats.hbm_in_use -= rq.bytes;
             srv->stats.completed++;
             srv->stats.active--;
+            if (rq.qubits >= srv->large_qubits) srv->active_large--;
             rq.phase = 2;
             rq.t_end = Clock::now();
             sl.busy = false;
@@ -2134,11 +2137,13 @@ void serve_worker(z2_server *srv) {
             progressed = true;
         }
         if (progressed) srv->cv_done.notify_all();
-        // admit in arrival order while a slot and the memory are free
-        while (!srv->queue.empty()) {
-            ServeReq &rq = srv->reqs[srv->queue.front()];
+        // admit in arrival order while a slot and the memory are free; a
+        // large run waiting only for a large-run place is passed over by the
+        // smaller runs behind it (it keeps its place in the queue)
+        for (auto qit = srv->queue.begin(); qit != srv->queue.end();) {
+            ServeReq &rq = srv->reqs[*qit];
             if (rq.phase == 3) {  // cancelled while queued
-                srv->queue.pop_front();
+                qit = srv->queue.erase(qit);
                 srv->stats.queued--;
                 continue;
             }
@@ -2149,8 +2154,14 @@ void serve_worker(z2_server *srv) {
                     break;
                 }
             if (!free_slot || srv->stats.hbm_in_use + rq.bytes > srv->budget) break;
-            srv->queue.pop_front();
+            const bool large = rq.qubits >= srv->large_qubits;
+            if (large && srv->active_large >= srv->max_large) {
+                ++qit;
+                continue;
+            }
+            qit = srv->queue.erase(qit);
             srv->stats.queued--;
+            if (large) srv->active_large++;
             rq.phase = 1;
             rq.t_start = Clock::now();
             srv->stats.active++;
@@ -2185,12 +2196,16 @@ void serve_worker(z2_server *srv) {
                 r2.t_end = Clock::now();
                 srv->stats.hbm_in_use -= r2.bytes;
                 srv->stats.active--;
+                if (r2.qubits >= srv->large_qubits) srv->active_large--;
                 srv->stats.completed++;
                 sl.busy = false;
                 sl.state = nullptr;
                 srv->cv_done.notify_all();
             }
             progressed = true;
+            // the lock was released: the queue may have grown (its iterators
+            // are invalid), so the scan starts again from the front
+            qit = srv->queue.begin();
         }
         const bool any_busy = std::any_of(srv->slots.begin(), srv->slots.end(), [](const ServeSlot &x) { return x.busy; });
         if (srv->stopping && !any_busy && srv->queue.empty()) break;
@@ -2282,6 +2297,7 @@ int z2_server_submit(z2_server *srv, const z2_run_spec *spec, uint64_t *ticket) 
     rq.id = srv->next_id++;
     rq.spec = *spec;
     rq.bytes = bytes;
+    rq.qubits = probe.n_links;
     rq.t_submit = Clock::now();
     srv->reqs[rq.id] = rq;
     srv->queue.push_back(rq.id);
@@ -2340,6 +2356,23 @@ int z2_server_request_times(z2_server *srv, uint64_t ticket, double *queued_s, d
     if (rq.phase != 2) return Z2_ERR_ARG;
     *queued_s = std::chrono::duration<double>(rq.t_start - rq.t_submit).count();
     *run_s = std::chrono::duration<double>(rq.t_end - rq.t_start).count();
+    return Z2_OK;
+}
+
+int z2_server_set_option(z2_server *srv, int32_t option, int32_t value) {
+    if (!srv) return Z2_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (option == Z2_SERVE_OPT_LARGE_QUBITS) {
+        if (value < 1 || value > Z2_MAX_LINKS + 1) return Z2_ERR_ARG;
+        if (srv->stats.active > 0) return Z2_ERR_ARG;  // classes change only while nothing runs
+        srv->large_qubits = value;
+    } else if (option == Z2_SERVE_OPT_MAX_LARGE) {
+        if (value < 1 || value > 64) return Z2_ERR_ARG;
+        srv->max_large = value;
+    } else {
+        return Z2_ERR_ARG;
+    }
+    srv->cv_work.notify_one();
     return Z2_OK;
 }
 

@@ -50,7 +50,7 @@ def test_kernel_names_follow_the_plan():
     assert bench.kernel_name(2, _info(13, 13, 3)) == "pass_kernel_tma<float2,13,RX>"
     assert bench.kernel_name(1, _info(14, 14, 3)) == "pass_kernel_packed<14,4,RX>"
     assert bench.kernel_name(0, _info(14, 14, 2)) == "pass_kernel_packed<14,4,RX>"
-    assert bench.kernel_name(0, _info(14, 13, 2)) == "pass_kernel_ring<13,4,RX>+pass_kernel_packed<14,4,RX>"
+    assert bench.kernel_name(0, _info(13, 13, 2)) == "pass_kernel_ring<13,4,RX>+<13,5,RX>"
 
 
 def test_traffic_record_checks_kernel_and_source(tmp_path, monkeypatch):

@@ -131,3 +131,30 @@ def test_serve_budget_and_cancel(ctx):
         assert st.rejected == 1 and st.cancelled == 1 and st.completed == 5
     finally:
         z2.z2_server_destroy(srv)
+
+
+def test_size_classes_large_runs_take_turns(ctx):
+    # With one large-run place, two 24-qubit runs never share the GPU: the
+    # second one's first kernel runs after the first one's work has ended.
+    # A small run submitted after both passes the waiting one and runs beside
+    # the first (device-clock events on the runs' streams).
+    srv = z2.z2_server_create(ctx, hbm_budget=1 << 30, max_slots=4)
+    try:
+        z2.z2_server_set_option(srv, z2.Z2_SERVE_OPT_MAX_LARGE, 1)
+        big = dict(d=2, L=(4, 3), lam=2.0, T=8.0, M=200)
+        small = dict(d=2, L=(3, 3), lam=1.0, T=2.0, M=50)
+        tbig = [z2.z2_server_submit(srv, big) for _ in range(2)]
+        tsmall = z2.z2_server_submit(srv, small)
+        for tk in tbig + [tsmall]:
+            rc, res = z2.z2_server_wait(srv, tk, timeout_s=120)
+            assert rc == 0 and abs(res.norm - 1) < 1e-5
+        (a0, a1), (b0, b1) = (z2.z2_server_request_device_times(srv, tk) for tk in tbig)
+        s0, s1 = z2.z2_server_request_device_times(srv, tsmall)
+        assert b0 > a1, ((a0, a1), (b0, b1))
+        assert s0 < a1, ((a0, a1), (s0, s1))
+        with pytest.raises(z2.Z2Error):
+            z2.z2_server_set_option(srv, z2.Z2_SERVE_OPT_MAX_LARGE, 0)
+        with pytest.raises(z2.Z2Error):
+            z2.z2_server_set_option(srv, 7, 1)
+    finally:
+        z2.z2_server_destroy(srv)

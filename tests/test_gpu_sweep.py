@@ -86,7 +86,7 @@ def test_sweep_errors(ctx):
 
 
 def test_persistent_sweep(ctx):
-    # runs of >= 14 qubits go through the one persistent launch (2^14-amplitude
+    # runs of 14 to 21 qubits go through the one persistent launch (2^14-amplitude
     # tiles, direct kernel arithmetic), the others through the normal path
     specs = small_specs(16, seed=11)
     res = z2.z2_sweep(ctx, specs, mode=z2.Z2_SWEEP_PERSISTENT, n_streams=4)

@@ -62,7 +62,9 @@ def check_plan(n, tile_bits, variant, tma):
             assert g.c == g.b == g.tile_bits and 1 <= g.k <= g.tile_bits
         else:
             assert g.c + g.k == g.tile_bits, "a strided tile is its passengers plus its rotated bits"
-            assert 3 <= g.c <= 8 and g.b >= g.c
+            # at least 3 passenger bits (64-byte rows), except the 24-qubit ring
+            # rule's 2 (32-byte rows, on a state about the size of L2)
+            assert (g.c >= 3 or (n == 24 and g.c == 2 and g.tile_bits == 13)) and g.c <= 8 and g.b >= g.c
             if g.k1 < g.k:
                 assert 1 <= g.k1 <= 8 and 1 <= g.k - g.k1 <= 8
                 assert g.b2 >= g.b + g.k1 and g.b2 + g.k - g.k1 == n, "the upper range ends at the top bit"
@@ -122,18 +124,18 @@ def test_no_extra_pass_for_the_smaller_low_tile():
             assert len(check_plan(n, tb, 3, True)) == len(check_plan(n, tb, 3, False))
 
 
-def test_24_qubit_mixed_plan():
-    # 24 qubits: the low group on a 13-bit ring tile, the 11 strided bits on a
-    # 14-bit direct-kernel tile with 3 passenger bits (64-byte rows); one merged
-    # pass per Trotter step either way.  Forced 14-bit tiles, another variant or
-    # no tensor-map encoder keep the 14 + 10 plan.
+def test_24_qubit_ring_plan():
+    # 24 qubits: both groups on 13-bit ring tiles, the 11 strided bits with 2
+    # passenger bits (32-byte rows); one merged pass per Trotter step.  Forced
+    # 14-bit tiles, another variant or no tensor-map encoder keep the 14 + 10
+    # plan on the direct kernel; other sizes keep 3 or more passenger bits.
     g = check_plan(24, 0, 0, True)
-    assert [(x.tile_bits, x.c, x.b, x.k) for x in g] == [(13, 13, 13, 13), (14, 3, 13, 11)]
+    assert [(x.tile_bits, x.c, x.b, x.k) for x in g] == [(13, 13, 13, 13), (13, 2, 13, 11)]
     for tb, variant, tma in ((14, 0, True), (0, 1, True), (0, 0, False)):
         g = check_plan(24, tb, variant, tma)
         assert [(x.tile_bits, x.k) for x in g] == [(14, 14), (14, 10)]
-    for n in (22, 23, 25):  # other sizes keep their plans
-        assert check_plan(n, 0, 0, True)[0].tile_bits != 13 or n == 23
+    for n in (20, 22, 23, 25, 26):
+        assert all(x.c >= 3 for x in check_plan(n, 0, 0, True)[1:])
 
 
 def test_rejects_bad_arguments():
