@@ -8,7 +8,8 @@ step by step onto 2^{N_p}-dimensional spin simulations:
 lambda = 3, T = 20, M = 500, first order and symmetric, complex64 state,
 the same launch configuration the benchmark times.  Fidelity is against the
 dual ground state lifted to the link basis (sigma^x basis amplitudes
-sqrt(2) phi(tau) on the configurations x_l = tau_p tau_q).
+sqrt(2) phi(tau) on the configurations x_l = tau_p tau_q).  The 24-qubit
+case is also checked against the direct FP64 state-vector oracle.
 """
 
 import math
@@ -83,3 +84,28 @@ def test_against_dual(ctx, L, decomp):
     assert abs(F - F_ref) < 1e-6, (F, F_ref, d["norm"], abs(ov) ** 2)
     del g
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("decomp", [1, 0])
+def test_24_qubit_subcase_against_direct_oracle(ctx, decomp):
+    # the 32-qubit configuration's 24-qubit sub-case (4x3, lambda = 3, T = 20,
+    # M = 500, both splits) against the direct FP64 state-vector oracle, not
+    # only through the duality: every observable, and the state's fidelity
+    # loss (<= 1e-6)
+    lam, T, M = 3.0, 20.0, 500
+    ol = OLattice(2, (4, 3))
+    psi = oracle.run(ol, lam, T, M, decomp)
+    ref = oracle.observables(ol, psi, lam)
+    lat = z2.Lattice(2, (4, 3))
+    g = torch.empty(1 << 24, dtype=torch.complex64, device="cuda")
+    res = z2.z2_run(ctx, lat.handle, z2.params(lam, T, M, decomp, z2.Z2_C64), g)
+    d = z2.results_dict(res, lat.info)
+    S = ol.n_links + lam * ol.n_plaq
+    assert abs(d["energy"] - ref["energy"]) < 1e-5 * S
+    for k in ("plaq", "sigmax", "sigmaz", "star", "wmu", "vmu"):
+        assert np.max(np.abs(d[k] - ref[k])) < 1e-5, k
+    assert abs(d["wilson_2x2"] - ref["wilson_2x2"]) < 1e-5
+    torch.cuda.synchronize()
+    got = g.cpu().numpy().astype(np.complex128)
+    f = abs(np.vdot(psi, got)) ** 2 / (np.vdot(psi, psi).real * np.vdot(got, got).real)
+    assert 1 - f < 1e-6, 1 - f
