@@ -207,10 +207,33 @@ __device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], 
     }
 }
 
+// Pair phase table of a plaquette layer.  The two amplitudes x and x^1 of a
+// pair have the parity vectors p and p ^ c0, c0 the plaquette column of
+// global bit 0, so their phase indices are k0 = popcount(p) and
+// k1 = popcount(p ^ c0) = k0 + popcount(c0) - 2 d with d = popcount(p & c0).
+// Entry 8 k0 + d holds both phases as the two packed halves the butterflies
+// use, (re(tab[k0]), re(tab[k1])) and (im(tab[k0]), im(tab[k1])): one 16-byte
+// load per pair in place of four scalar loads.  A link lies in at most
+// 2 (dim - 1) = 4 plaquettes, so d < 8; combinations that cannot occur (k1
+// outside the table) hold a clamped entry that is never read.
+constexpr int PAIR_TAB_ENTRIES = (Z2_MAX_PLAQ + 1) * 8;
+
+__device__ __forceinline__ void load_pair_table(ulonglong2 *ptab, const float2 *tab, int np1, uint32_t c0,
+                                                uint32_t tid, uint32_t nth) {
+    const int w = __popc(c0);
+    for (uint32_t e = tid; e < (uint32_t)np1 * 8u; e += nth) {
+        const int k0 = (int)(e >> 3), d = (int)(e & 7u);
+        int k1 = k0 + w - 2 * d;
+        k1 = k1 < 0 ? 0 : (k1 >= np1 ? np1 - 1 : k1);
+        const float2 x = tab[k0], y = tab[k1];
+        ptab[e] = make_ulonglong2(pk2(x.x, y.x), pk2(x.y, y.y));
+    }
+}
+
 // plaquette phase table or real scale, in layout Q
 template <int TB, int W, int Q>
 __device__ __forceinline__ void pmid(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassArgs &a, int mid, double scale,
-                                     uint32_t ptile, uint32_t t, const float *tabr, const float *tabi) {
+                                     uint32_t ptile, uint32_t t, const ulonglong2 *ptab) {
     using T = PTile<TB, W>;
     if (mid == MID_SCALE) {
         const float s = (float)scale;
@@ -233,8 +256,8 @@ __device__ __forceinline__ void pmid(u64 (&re)[1 << W], u64 (&im)[1 << W], const
         for (int gi = 0; gi < T::NP; ++gi) {
             if (gi) p ^= a.tcol[r + ctz_c(gi) + 1];
             const int j = gi ^ (gi >> 1);
-            const int k0 = __popc(p), k1 = __popc(p ^ c0);
-            const u64 tr = pk2(tabr[k0], tabr[k1]), ti = pk2(tabi[k0], tabi[k1]);
+            const ulonglong2 e = ptab[((uint32_t)__popc(p) << 3) | (uint32_t)__popc(p & c0)];
+            const u64 tr = e.x, ti = e.y;
             const u64 nre = sub2(mul2(re[j], tr), mul2(im[j], ti));
             const u64 nim = fma2(re[j], ti, mul2(im[j], tr));
             re[j] = nre;
@@ -257,14 +280,13 @@ __device__ __forceinline__ void prot_in(int q, u64 (&re)[1 << W], u64 (&im)[1 <<
 
 template <int TB, int W>
 __device__ __forceinline__ void pmid_in(int q, u64 (&re)[1 << W], u64 (&im)[1 << W], const PassArgs &a, int mid,
-                                        double scale, uint32_t ptile, uint32_t t, const float *tabr,
-                                        const float *tabi) {
+                                        double scale, uint32_t ptile, uint32_t t, const ulonglong2 *ptab) {
     constexpr int K = PTile<TB, W>::K;
     switch (q) {
-        case 0: pmid<TB, W, 0>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
-        case 1: pmid<TB, W, (1 < K ? 1 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
-        case 2: pmid<TB, W, (2 < K ? 2 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
-        default: pmid<TB, W, (3 < K ? 3 : 0)>(re, im, a, mid, scale, ptile, t, tabr, tabi); break;
+        case 0: pmid<TB, W, 0>(re, im, a, mid, scale, ptile, t, ptab); break;
+        case 1: pmid<TB, W, (1 < K ? 1 : 0)>(re, im, a, mid, scale, ptile, t, ptab); break;
+        case 2: pmid<TB, W, (2 < K ? 2 : 0)>(re, im, a, mid, scale, ptile, t, ptab); break;
+        default: pmid<TB, W, (3 < K ? 3 : 0)>(re, im, a, mid, scale, ptile, t, ptab); break;
     }
 }
 
@@ -295,8 +317,8 @@ __device__ __forceinline__ void prelayout_rt(int qa, int qb, u64 (&re)[1 << W], 
 // one pass step on the registers of a tile (layout 0 in and out)
 template <int TB, int W, int OP, bool S8 = false>
 __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st, const PassArgs &a,
-                                      float g1, float g2, uint32_t ptile, uint32_t t, ulonglong2 *sm, const float *tabr,
-                                      const float *tabi, int bar) {
+                                      float g1, float g2, uint32_t ptile, uint32_t t, ulonglong2 *sm,
+                                      const ulonglong2 *ptab, int bar) {
     using T = PTile<TB, W>;
     int cur = 0;
     prot_in<TB, W, OP>(0, re, im, st.rot1, g1);
@@ -308,7 +330,7 @@ __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], cons
             prot_in<TB, W, OP>(q, re, im, st.rot1, g1);
         }
     }
-    pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
+    pmid_in<TB, W>(cur, re, im, a, st.mid, st.scale, ptile, t, ptab);
     if (st.rot2 == 0) {  // no second rotation (uniform over the launch): back to layout 0
         if (cur != 0) prelayout_rt<TB, W, S8>(cur, 0, re, im, sm, t, bar);
         return;
@@ -361,11 +383,11 @@ __device__ __forceinline__ void seq_down(u64 (&re)[1 << W], u64 (&im)[1 << W], c
 template <int TB, int W, int OP, bool S8, int L, bool R2>
 __device__ __forceinline__ void pstep_static(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st,
                                              const PassArgs &a, float g1, float g2, uint32_t ptile, uint32_t t,
-                                             ulonglong2 *sm, const float *tabr, const float *tabi, int bar) {
+                                             ulonglong2 *sm, const ulonglong2 *ptab, int bar) {
     static_assert(L >= 1 && L <= PTile<TB, W>::K, "static sequence beyond the tile's layouts");
     prot<TB, W, 0, OP>(re, im, st.rot1, g1);
     seq_up<TB, W, OP, S8, 1, L>(re, im, st, g1, sm, t, bar);
-    pmid<TB, W, L - 1>(re, im, a, st.mid, st.scale, ptile, t, tabr, tabi);
+    pmid<TB, W, L - 1>(re, im, a, st.mid, st.scale, ptile, t, ptab);
     if constexpr (R2) {
         prot<TB, W, L - 1, OP>(re, im, L - 1 == 0 ? st.rot2 : (st.rot2 & ~1u), g2);
         seq_down<TB, W, OP, S8, L - 2>(re, im, st, g2, sm, t, bar);
@@ -401,7 +423,7 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
     using T = PTile<TB, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ulonglong2 *sm = reinterpret_cast<ulonglong2 *>(smem_raw);
-    __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
+    __shared__ ulonglong2 ptab[PAIR_TAB_ENTRIES];
 
     const uint32_t t = threadIdx.x;
     const int c = a.c, b = a.b;
@@ -449,14 +471,10 @@ __global__ void __launch_bounds__(PTile<TB, W>::NT, PTile<TB, W>::MINB)
             const PassStep st = steps[s];
             if (st.mid == MID_TABLE) {
                 __syncthreads();
-                for (uint32_t q = t; q < (uint32_t)a.np1; q += T::NT) {
-                    const float2 e = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
-                    tabr[q] = e.x;
-                    tabi[q] = e.y;
-                }
+                load_pair_table(ptab, tables + (size_t)st.table * (Z2_MAX_PLAQ + 1), a.np1, a.tcol[0], t, T::NT);
                 __syncthreads();
             }
-            pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, -1);
+            pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, ptab, -1);
         }
         uint64_t off = g0 + gthr;
         asm volatile("" : "+l"(off));
@@ -513,6 +531,18 @@ __device__ __forceinline__ bool bar_and(int bar, int n, bool v) {
     return r != 0;
 }
 
+// Plaquette parity vector of the amplitude at global index g0: the XOR of the
+// columns of g0's set bits.  The 64 bits are shared out over the lanes of a
+// warp (lane l takes bits l and l + 32) and the warp XOR-reduces, so every
+// lane gets the result in a dozen instructions instead of a serial loop over
+// the set bits in every thread.  All 32 lanes must take part.
+__device__ __forceinline__ uint32_t warp_tile_parity(uint64_t g0, const uint32_t *colm, uint32_t lane) {
+    uint32_t v = (((g0 >> lane) & 1ull) ? colm[lane] : 0u) ^ (((g0 >> (lane + 32)) & 1ull) ? colm[lane + 32] : 0u);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <int TB, int W, int OP, bool S8 = false, int SEQ = 0>
 __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     pass_kernel_ring(const __grid_constant__ PassArgs a, const __grid_constant__ CUtensorMap tmap,
@@ -520,12 +550,14 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     using T = PTile<TB, W>;
     using RT = RingTile<TB, W>;
     constexpr int NW = RT::NW, NB = RT::NB;
+    static_assert(T::NT % 32 == 0, "ring workers are whole warps (the tile parity is a warp reduction)");
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[NB];
     __shared__ uint32_t loads_issued[NB];  // TMA loads issued into each buffer
     __shared__ uint32_t uses_seen[NB];     // loads of each buffer whose completion a worker has observed
     __shared__ int abort_s;                // a worker gave up waiting
-    __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
+    __shared__ ulonglong2 ptab[PAIR_TAB_ENTRIES];
+    __shared__ uint32_t colm_s[64];        // plaquette column of each global bit
     // 1024-byte aligned start, as an offset into the shared array (keeps the
     // accesses in the shared address space)
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -549,11 +581,9 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
     };
 
     if (st.mid == MID_TABLE)
-        for (uint32_t q = threadIdx.x; q < (uint32_t)a.np1; q += NW * T::NT) {
-            const float2 e = tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
-            tabr[q] = e.x;
-            tabi[q] = e.y;
-        }
+        load_pair_table(ptab, tables + (size_t)st.table * (Z2_MAX_PLAQ + 1), a.np1, a.tcol[0], threadIdx.x,
+                        NW * T::NT);
+    for (uint32_t q = threadIdx.x; q < 64u; q += NW * T::NT) colm_s[q] = a.colmask[q];
     if (threadIdx.x == 0) {
         for (int k = 0; k < NB; ++k) {
             mbar_init(&mbar[k], 1);
@@ -601,8 +631,7 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
         const uint64_t tile = gtile(n);
         const uint64_t tlo = tile & ((1ull << (b - c)) - 1ull);
         const uint64_t g0 = (tlo << c) | ((tile >> (b - c)) << hib);
-        uint32_t ptile = 0;
-        for (uint64_t m = g0; m; m &= m - 1) ptile ^= a.colmask[__ffsll((long long)m) - 1];
+        const uint32_t ptile = warp_tile_parity(g0, colm_s, threadIdx.x & 31u);
 
         ulonglong2 *sm = buf(bi);
         u64 re[T::NP], im[T::NP];
@@ -625,10 +654,10 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
         }
         tile_sync<T::NT>(bar);  // dense reads done before the padded layouts reuse the buffer
         if constexpr (SEQ == 0)
-            pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, bar);
+            pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, ptab, bar);
         else
             pstep_static<TB, W, OP, S8, SEQ / 2, (SEQ & 1) != 0>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t,
-                                                                 sm, tabr, tabi, bar);
+                                                                 sm, ptab, bar);
         tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
         if (out_split) {
 #pragma unroll

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
     using T = PTile<TB, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ulonglong2 *sm = reinterpret_cast<ulonglong2 *>(smem_raw);
-    __shared__ float tabr[Z2_MAX_PLAQ + 1], tabi[Z2_MAX_PLAQ + 1];
+    __shared__ ulonglong2 ptab[PAIR_TAB_ENTRIES];
     __shared__ PassArgs a_s;
     __shared__ unsigned long long run_s;
 
@@ -157,14 +157,11 @@ __global__ void __launch_bounds__(PTile<PERSIST_TB, PERSIST_W>::NT, 1)
                     const PassStep st = steps[s];
                     if (st.mid == MID_TABLE) {
                         __syncthreads();
-                        for (uint32_t q = t; q < (uint32_t)a.np1; q += T::NT) {
-                            const float2 e = R.tables[(size_t)st.table * (Z2_MAX_PLAQ + 1) + q];
-                            tabr[q] = e.x;
-                            tabi[q] = e.y;
-                        }
+                        load_pair_table(ptab, R.tables + (size_t)st.table * (Z2_MAX_PLAQ + 1), a.np1, a.tcol[0], t,
+                                        T::NT);
                         __syncthreads();
                     }
-                    pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, tabr, tabi, -1);
+                    pstep<TB, W, OP>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, ptab, -1);
                 }
                 float2 *q = R.state + g0 + gthr;
                 if (out_split) {
