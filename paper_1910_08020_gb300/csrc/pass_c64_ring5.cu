@@ -52,7 +52,11 @@ cudaError_t launch_pass_ring5_c64(int tb, int op, const PassArgs &a, const void 
         return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 12 && seq == seq_code(2, true))
         return launch_ring5_tb<12, OP_RX_TAN, true, seq_code(2, true)>(a, m, ps, tab, fmt, err, grid, st);
-    // the 24-qubit strided group (two passenger bits): its bits reach layout 2
+    // the 24-qubit strided group (two passenger bits): its one rotated bit
+    // beyond layout 1 is a lane bit there, rotated by warp shuffles
+    if (s8 && op == OP_RX_TAN && tb == 13 && seq == seq_code(2, true, 2))
+        return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(2, true, 2)>(a, m, ps, tab, fmt, err, grid, st);
+    // a strided group whose bits reach layout 2 otherwise
     if (s8 && op == OP_RX_TAN && tb == 13 && seq == seq_code(3, true))
         return launch_ring5_tb<13, OP_RX_TAN, true, seq_code(3, true)>(a, m, ps, tab, fmt, err, grid, st);
     if (s8 && op == OP_RX_TAN && tb == 12)

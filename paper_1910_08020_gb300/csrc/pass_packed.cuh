@@ -351,6 +351,36 @@ __device__ __forceinline__ void pstep(u64 (&re)[1 << W], u64 (&im)[1 << W], cons
     }
 }
 
+// Rotation levels on pair-index bits that are lane bits of register layout
+// Q.  In layout Q the pair-index bits below w0(Q) are the low bits of the
+// thread index, so bit i < 5 there pairs lane l with lane l ^ (1 << i) of the
+// same warp, for every register pair alike.  The butterfly is symmetric,
+// (a, b) -> (a + i t b, b + i t a): each lane adds i t times its partner's
+// amplitude, with the partner's (re, re) and (im, im) halves fetched by warp
+// shuffles.  The arithmetic is that of bfly2, so results are bit-identical to
+// a visit of the layout that holds the bit in registers, without its two
+// relayouts.  LB is the mask of such pair-index bits; a bit that the pass does
+// not rotate gets gate 0 (an exact identity).
+template <int TB, int W, int Q, int OP, int LB>
+__device__ __forceinline__ void prot_lanes(u64 (&re)[1 << W], u64 (&im)[1 << W], uint32_t mask, float t) {
+    using T = PTile<TB, W>;
+    static_assert(OP == OP_RX_TAN, "lane levels are transverse-field rotations");
+    static_assert((LB >> (T::w0(Q) < 5 ? T::w0(Q) : 5)) == 0, "lane levels need lane bits of the layout");
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        if (!((LB >> i) & 1)) continue;
+        const float g = ((mask >> (i + 1)) & 1u) ? t : 0.0f;
+        const u64 tq = pk2(g, g), mq = pk2(-g, -g);
+#pragma unroll
+        for (int j = 0; j < T::NP; ++j) {
+            const u64 rp = __shfl_xor_sync(0xffffffffu, re[j], 1 << i);
+            const u64 ip = __shfl_xor_sync(0xffffffffu, im[j], 1 << i);
+            re[j] = fma2(mq, ip, re[j]);
+            im[j] = fma2(tq, rp, im[j]);
+        }
+    }
+}
+
 // Static layout sequences.  pstep chooses at run time which register
 // layouts a pass visits; the join points of those choices cost register
 // moves.  When the host knows that rot1 and rot2 lie in the register bits of
@@ -380,15 +410,17 @@ __device__ __forceinline__ void seq_down(u64 (&re)[1 << W], u64 (&im)[1 << W], c
     }
 }
 
-template <int TB, int W, int OP, bool S8, int L, bool R2>
+template <int TB, int W, int OP, bool S8, int L, bool R2, int LB = 0>
 __device__ __forceinline__ void pstep_static(u64 (&re)[1 << W], u64 (&im)[1 << W], const PassStep &st,
                                              const PassArgs &a, float g1, float g2, uint32_t ptile, uint32_t t,
                                              ulonglong2 *sm, const ulonglong2 *ptab, int bar) {
     static_assert(L >= 1 && L <= PTile<TB, W>::K, "static sequence beyond the tile's layouts");
     prot<TB, W, 0, OP>(re, im, st.rot1, g1);
     seq_up<TB, W, OP, S8, 1, L>(re, im, st, g1, sm, t, bar);
+    if constexpr (LB != 0) prot_lanes<TB, W, L - 1, OP, LB>(re, im, st.rot1, g1);
     pmid<TB, W, L - 1>(re, im, a, st.mid, st.scale, ptile, t, ptab);
     if constexpr (R2) {
+        if constexpr (LB != 0) prot_lanes<TB, W, L - 1, OP, LB>(re, im, st.rot2, g2);
         prot<TB, W, L - 1, OP>(re, im, L - 1 == 0 ? st.rot2 : (st.rot2 & ~1u), g2);
         seq_down<TB, W, OP, S8, L - 2>(re, im, st, g2, sm, t, bar);
     } else if constexpr (L > 1) {
@@ -396,8 +428,9 @@ __device__ __forceinline__ void pstep_static(u64 (&re)[1 << W], u64 (&im)[1 << W
     }
 }
 
-// SEQ template argument of the ring kernel: 0 = pstep, else 2 L + R2
-constexpr int seq_code(int L, bool R2) { return 2 * L + (R2 ? 1 : 0); }
+// SEQ template argument of the ring kernel: 0 = pstep, else 2 L + R2, plus
+// 16 LB for lane levels (prot_lanes) in layout L - 1
+constexpr int seq_code(int L, bool R2, int lb = 0) { return 2 * L + (R2 ? 1 : 0) + 16 * lb; }
 
 // Ask the TMA unit to pull a tile into L2 ahead of its use (no completion is
 // tracked: a prefetch never blocks and never faults on in-range addresses).
@@ -656,8 +689,8 @@ __global__ void __launch_bounds__(RingTile<TB, W>::NW * PTile<TB, W>::NT, 1)
         if constexpr (SEQ == 0)
             pstep<TB, W, OP, S8>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, ptab, bar);
         else
-            pstep_static<TB, W, OP, S8, SEQ / 2, (SEQ & 1) != 0>(re, im, st, a, (float)st.g1, (float)st.g2, ptile, t,
-                                                                 sm, ptab, bar);
+            pstep_static<TB, W, OP, S8, (SEQ & 15) / 2, (SEQ & 1) != 0, (SEQ >> 4)>(
+                re, im, st, a, (float)st.g1, (float)st.g2, ptile, t, sm, ptab, bar);
         tile_sync<T::NT>(bar);  // padded reads done before the dense store image is written
         if (out_split) {
 #pragma unroll

@@ -581,13 +581,24 @@ uint32_t layout_own_bits(int tb, int W, int q) {
 
 // Static layout sequence of a ring pass (pstep_static): the fewest layouts
 // 0 .. L-1 that hold every rotated bit of rot1 and rot2, coded 2 L + (rot2 != 0).
+// The wide kernel's 13-bit strided pass whose only rotated bit beyond layout 1
+// is pair-index bit 1 (a group with two passenger bits) rotates that bit by
+// warp shuffles in layout 1, where it is lane bit 1 (code + 16 * lane mask):
+// two relayouts instead of four.
 int ring_seq(int tb, int W, const PassStepHost &s) {
     const int Y = tb - 1, K = (Y + W - 1) / W;
     const uint32_t bits = (s.rot1 | s.rot2) >> 1;
+    const int r2 = s.rot2 ? 1 : 0;
     uint32_t cover = 0;
     for (int L = 1; L <= K; ++L) {
         cover |= layout_own_bits(tb, W, L - 1);
-        if (!(bits & ~cover)) return 2 * L + (s.rot2 ? 1 : 0);
+        if (!(bits & ~cover)) {
+            if (W == 5 && tb == 13 && L == 3) {
+                const uint32_t rest = bits & ~(layout_own_bits(tb, W, 0) | layout_own_bits(tb, W, 1));
+                if (rest == 2u) return 2 * 2 + r2 + 16 * 2;
+            }
+            return 2 * L + r2;
+        }
     }
     return 0;
 }
