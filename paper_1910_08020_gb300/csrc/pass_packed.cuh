@@ -211,18 +211,24 @@ __device__ __forceinline__ void prelayout(u64 (&re)[1 << W], u64 (&im)[1 << W], 
 // pair have the parity vectors p and p ^ c0, c0 the plaquette column of
 // global bit 0, so their phase indices are k0 = popcount(p) and
 // k1 = popcount(p ^ c0) = k0 + popcount(c0) - 2 d with d = popcount(p & c0).
-// Entry 8 k0 + d holds both phases as the two packed halves the butterflies
-// use, (re(tab[k0]), re(tab[k1])) and (im(tab[k0]), im(tab[k1])): one 16-byte
-// load per pair in place of four scalar loads.  A link lies in at most
-// 2 (dim - 1) = 4 plaquettes, so d < 8; combinations that cannot occur (k1
-// outside the table) hold a clamped entry that is never read.
-constexpr int PAIR_TAB_ENTRIES = (Z2_MAX_PLAQ + 1) * 8;
+// Entry k0 + PAIR_TAB_STRIDE d holds both phases as the two packed halves the
+// butterflies use, (re(tab[k0]), re(tab[k1])) and (im(tab[k0]), im(tab[k1])):
+// one 16-byte load per pair in place of four scalar loads.  The stride is 1
+// modulo 8, so entry (k0, d) sits in bank group (k0 + d) mod 8 and the lanes
+// of a quarter warp, whose k0 differ, mostly hit distinct banks (with the
+// index 8 k0 + d every lane of equal d shared four banks).  A link lies in at
+// most 2 (dim - 1) = 4 plaquettes, so d < 8; combinations that cannot occur
+// (k1 outside the table) hold a clamped entry that is never read.
+constexpr int PAIR_TAB_STRIDE = Z2_MAX_PLAQ + 1;
+static_assert(PAIR_TAB_STRIDE % 8 == 1, "pair-table stride must be 1 modulo 8");
+constexpr int PAIR_TAB_ENTRIES = PAIR_TAB_STRIDE * 8;
 
 __device__ __forceinline__ void load_pair_table(ulonglong2 *ptab, const float2 *tab, int np1, uint32_t c0,
                                                 uint32_t tid, uint32_t nth) {
     const int w = __popc(c0);
-    for (uint32_t e = tid; e < (uint32_t)np1 * 8u; e += nth) {
-        const int k0 = (int)(e >> 3), d = (int)(e & 7u);
+    for (uint32_t e = tid; e < (uint32_t)PAIR_TAB_ENTRIES; e += nth) {
+        const int k0 = (int)(e % PAIR_TAB_STRIDE), d = (int)(e / PAIR_TAB_STRIDE);
+        if (k0 >= np1) continue;
         int k1 = k0 + w - 2 * d;
         k1 = k1 < 0 ? 0 : (k1 >= np1 ? np1 - 1 : k1);
         const float2 x = tab[k0], y = tab[k1];
@@ -256,7 +262,7 @@ __device__ __forceinline__ void pmid(u64 (&re)[1 << W], u64 (&im)[1 << W], const
         for (int gi = 0; gi < T::NP; ++gi) {
             if (gi) p ^= a.tcol[r + ctz_c(gi) + 1];
             const int j = gi ^ (gi >> 1);
-            const ulonglong2 e = ptab[((uint32_t)__popc(p) << 3) | (uint32_t)__popc(p & c0)];
+            const ulonglong2 e = ptab[(uint32_t)__popc(p) + PAIR_TAB_STRIDE * (uint32_t)__popc(p & c0)];
             const u64 tr = e.x, ti = e.y;
             const u64 nre = sub2(mul2(re[j], tr), mul2(im[j], ti));
             const u64 nim = fma2(re[j], ti, mul2(im[j], tr));
