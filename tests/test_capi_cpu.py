@@ -76,3 +76,33 @@ def test_mask_kind_error_and_version():
     with pytest.raises(z2.Z2Error):
         lat.masks(99)
     assert "sm_103a" in z2.z2_version()
+
+
+def _library_lattices():
+    """Every lattice shape the library builds within its limits (2D L in
+    2..17, 3D L in 2..3), found by asking it."""
+    out = []
+    for d, Ls in [(2, [(a, b) for a in range(2, 18) for b in range(2, 18)]),
+                  (3, [(a, b, c) for a in (2, 3) for b in (2, 3) for c in (2, 3)])]:
+        for L in Ls:
+            try:
+                lat = z2.Lattice(d, L)
+            except Exception:
+                continue
+            out.append((d, L, lat.masks(z2.Z2_MASK_PLAQ), lat.n_links))
+            lat.close()
+    return out
+
+
+def test_links_lie_in_few_plaquettes():
+    """The pass kernels look up both phases of an amplitude pair (x, x ^ 1) in
+    one table entry indexed by popcount(p) and popcount(p & c0), c0 the
+    plaquette column of link 0, and reserve 8 entries per popcount(p) for the
+    second index.  Every lattice the library builds keeps popcount(c0) at
+    2 (d - 1), each link in exactly that many distinct plaquettes."""
+    lats = _library_lattices()
+    assert any(d == 3 for d, _, _, _ in lats) and len(lats) > 10
+    for d, L, plaq, n_links in lats:
+        counts = [sum(1 for m in plaq if (int(m) >> l) & 1) for l in range(n_links)]
+        assert max(counts) < 8, (d, L)
+        assert set(counts) == {2 * (d - 1)}, (d, L, set(counts))
