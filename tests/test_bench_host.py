@@ -77,3 +77,12 @@ def test_cpu_baseline_times_the_oracle_on_a_real_state():
     assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1
     assert "3x2 lattice (12 qubits" in cb["sample"] and "extrapolated" not in cb["sample"]
     assert cb["cpu"]
+
+
+def test_l2_note_for_states_near_the_l2_size():
+    """Inputs are not flushed between timed steps; the line says whether the
+    state dwarfs the 129 MB L2 or is about its size (24 qubits: part of every
+    pass is served from L2)."""
+    assert ">> L2" in bench.l2_note(8 << 32)
+    near = bench.l2_note(8 << 24)
+    assert "134 MB" in near and "about the size of L2" in near and ">>" not in near
